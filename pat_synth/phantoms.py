@@ -1,0 +1,203 @@
+"""Seeded phantom, sensor and noise generators (inputs only).
+
+All generators take a ``numpy.random.Generator`` built on PCG64 so that the
+same seed gives the same arrays on every machine.  Arrays are float64; the GPU
+side converts them to float32 when it uploads them.
+
+Index convention: a field on the N x N domain is ``[y][x]`` with x fastest;
+cell (iy, ix) has its centre at ((ix + 0.5) dx, (iy + 0.5) dx) in the domain
+frame, whose origin is the domain's lower-left corner.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+
+def rng_for(seed: int) -> np.random.Generator:
+    """PCG64 generator for ``seed``."""
+    return np.random.Generator(np.random.PCG64(int(seed)))
+
+
+def _cell_coords(n: int):
+    """Cell-centre coordinates in cells, origin at the domain centre."""
+    t = np.arange(n, dtype=np.float64) + 0.5 - n / 2.0
+    yy, xx = np.meshgrid(t, t, indexing="ij")
+    return xx, yy
+
+
+def ellipse_phantom(n: int, n_incl: int, rng: np.random.Generator,
+                    c_bg: float = 1500.0, c_range=(1400.0, 1650.0)) -> np.ndarray:
+    """Speed of sound: background ``c_bg`` plus ``n_incl`` elliptical inclusions.
+
+    Centres are uniform in a disc of radius 0.3 n, semi-axes uniform in
+    [0.05 n, 0.15 n], orientation uniform in [0, pi), value uniform in
+    ``c_range``; a later ellipse overwrites an earlier one where they overlap.
+    """
+    xx, yy = _cell_coords(n)
+    c = np.full((n, n), float(c_bg))
+    for _ in range(n_incl):
+        r = 0.3 * n * np.sqrt(rng.uniform())
+        phi = rng.uniform(0.0, 2.0 * np.pi)
+        cx, cy = r * np.cos(phi), r * np.sin(phi)
+        a = rng.uniform(0.05 * n, 0.15 * n)
+        b = rng.uniform(0.05 * n, 0.15 * n)
+        th = rng.uniform(0.0, np.pi)
+        val = rng.uniform(*c_range)
+        dx, dy = xx - cx, yy - cy
+        u = dx * np.cos(th) + dy * np.sin(th)
+        v = -dx * np.sin(th) + dy * np.cos(th)
+        c[(u / a) ** 2 + (v / b) ** 2 <= 1.0] = val
+    return c
+
+
+def blob_p0(n: int, n_blobs: int, rng: np.random.Generator,
+            amp=(0.5, 1.0), sigma_cells=(2.0, 5.0), radius_frac: float = 0.35) -> np.ndarray:
+    """Initial pressure made of ``n_blobs`` Gaussian blobs (summed).
+
+    Centres uniform in a disc of radius ``radius_frac`` n, amplitude and width
+    (in cells) uniform in the given ranges.
+    """
+    xx, yy = _cell_coords(n)
+    p0 = np.zeros((n, n))
+    for _ in range(n_blobs):
+        r = radius_frac * n * np.sqrt(rng.uniform())
+        phi = rng.uniform(0.0, 2.0 * np.pi)
+        cx, cy = r * np.cos(phi), r * np.sin(phi)
+        a = rng.uniform(*amp)
+        s = rng.uniform(*sigma_cells)
+        p0 += a * np.exp(-((xx - cx) ** 2 + (yy - cy) ** 2) / (2.0 * s * s))
+    return p0
+
+
+def vessel_p0(n: int, rng: np.random.Generator, n_seg=(3, 6), sigma_cells=(1.0, 2.5),
+              length_frac=(0.1, 0.4), amp=(0.5, 1.0), radius_frac: float = 0.35) -> np.ndarray:
+    """Vessel-like initial pressure: Gaussian line segments, summed, clipped at 1.
+
+    Each segment has a Gaussian cross-section of width U(sigma_cells) cells,
+    length U(length_frac) n, amplitude U(amp); its centre lies in a disc of
+    radius ``radius_frac`` n.
+    """
+    xx, yy = _cell_coords(n)
+    p0 = np.zeros((n, n))
+    for _ in range(int(rng.integers(n_seg[0], n_seg[1] + 1))):
+        r = radius_frac * n * np.sqrt(rng.uniform())
+        phi = rng.uniform(0.0, 2.0 * np.pi)
+        cx, cy = r * np.cos(phi), r * np.sin(phi)
+        th = rng.uniform(0.0, np.pi)
+        half = 0.5 * rng.uniform(*length_frac) * n
+        s = rng.uniform(*sigma_cells)
+        a = rng.uniform(*amp)
+        ex, ey = np.cos(th), np.sin(th)
+        dx, dy = xx - cx, yy - cy
+        along = np.clip(dx * ex + dy * ey, -half, half)
+        px, py = cx + along * ex, cy + along * ey
+        d2 = (xx - px) ** 2 + (yy - py) ** 2
+        p0 += a * np.exp(-d2 / (2.0 * s * s))
+    return np.minimum(p0, 1.0)
+
+
+def circle_sensors(n: int, m: int, dx: float, radius_cells: float | None = None,
+                   phase: float = 0.0) -> np.ndarray:
+    """``m`` point sensors evenly spaced on a circle about the domain centre.
+
+    Returns ``[m][2]`` (x, y) positions in metres in the domain frame (origin at
+    the lower-left corner of the N x N domain).  The default radius is
+    0.4375 n cells (28 cells at n = 64).
+    """
+    if radius_cells is None:
+        radius_cells = 0.4375 * n
+    ang = phase + 2.0 * np.pi * np.arange(m) / m
+    ctr = 0.5 * n * dx
+    xy = np.empty((m, 2))
+    xy[:, 0] = ctr + radius_cells * dx * np.cos(ang)
+    xy[:, 1] = ctr + radius_cells * dx * np.sin(ang)
+    return xy
+
+
+def add_noise(y_clean: np.ndarray, rng: np.random.Generator, rel: float = 0.01) -> np.ndarray:
+    """Additive Gaussian noise, std = ``rel`` x peak-to-peak of each data set.
+
+    ``y_clean`` is ``[K][Nt][M]``; data set k gets its own standard deviation
+    (Sec. 4.1.1: 1 % of the peak-to-peak amplitude of the simulated data).
+    """
+    y = np.asarray(y_clean, dtype=np.float64)
+    out = np.empty_like(y)
+    for k in range(y.shape[0]):
+        sig = rel * (y[k].max() - y[k].min())
+        out[k] = y[k] + sig * rng.standard_normal(y[k].shape)
+    return out
+
+
+def noise_weights(y_noisy: np.ndarray, rel: float = 0.01) -> np.ndarray:
+    """Per-data-set weights w_k = 1 / sigma_k^2 with sigma_k = rel x p2p(noisy y_k).
+
+    The noise model of the reconstruction uses the peak-to-peak amplitude of
+    the noisy signal (Sec. 4.1.2); L_e^T L_e = w_k I.
+    """
+    y = np.asarray(y_noisy, dtype=np.float64)
+    w = np.empty(y.shape[0])
+    for k in range(y.shape[0]):
+        sig = rel * (y[k].max() - y[k].min())
+        w[k] = 1.0 / (sig * sig) if sig > 0 else 1.0
+    return w
+
+
+@dataclass
+class Workload:
+    """One synthetic reconstruction problem (domain fields, float64)."""
+    n: int
+    dx: float
+    nt: int
+    c_true: np.ndarray            # [n][n]
+    p0_true: np.ndarray           # [K][n][n]
+    sensors: np.ndarray           # [M][2] metres
+    c_bg: float = 1500.0
+    c_bounds: tuple = (1350.0, 1750.0)
+    cfl: float = 0.3
+    seed: int = 0
+    extra: dict = field(default_factory=dict)
+
+    @property
+    def k(self) -> int:
+        return self.p0_true.shape[0]
+
+    @property
+    def m(self) -> int:
+        return self.sensors.shape[0]
+
+
+def workload(name: str, seed: int = 0) -> Workload:
+    """Named synthetic workloads.
+
+    * ``"plain64"``: 64 x 64, dx 0.1 mm, 3 ellipses, K = 1 with 5 blobs,
+      64 sensors on a circle of radius 28 cells, Nt = 400.
+    * ``"vessels128"``: 128 x 128, 6 ellipses, K = 4 vessel sets, 256 sensors,
+      Nt = 900 (dx 0.1 mm).
+    * ``"vessels256"``: 256 x 256, 6 ellipses, K = 8 vessel sets, 512 sensors,
+      Nt = 1800 (dx 0.1 mm).
+    * ``"tiny16"``: 16 x 16, K = 2, 12 sensors, Nt = 60 (finite-difference size).
+    """
+    rng = rng_for(seed)
+    dx = 1e-4
+    if name == "plain64":
+        n, K, M, nt = 64, 1, 64, 400
+        c = ellipse_phantom(n, 3, rng)
+        p0 = np.stack([blob_p0(n, 5, rng) for _ in range(K)])
+    elif name == "vessels128":
+        n, K, M, nt = 128, 4, 256, 900
+        c = ellipse_phantom(n, 6, rng)
+        p0 = np.stack([vessel_p0(n, rng) for _ in range(K)])
+    elif name == "vessels256":
+        n, K, M, nt = 256, 8, 512, 1800
+        c = ellipse_phantom(n, 6, rng)
+        p0 = np.stack([vessel_p0(n, rng) for _ in range(K)])
+    elif name == "tiny16":
+        n, K, M, nt = 16, 2, 12, 60
+        c = ellipse_phantom(n, 2, rng)
+        p0 = np.stack([blob_p0(n, 2, rng, sigma_cells=(1.5, 2.5)) for _ in range(K)])
+    else:
+        raise ValueError(f"unknown workload {name!r}")
+    sensors = circle_sensors(n, M, dx)
+    return Workload(n=n, dx=dx, nt=nt, c_true=c, p0_true=p0, sensors=sensors, seed=seed)
