@@ -1,0 +1,218 @@
+/*
+ * pat.h - C ABI of the GB300 library for joint reconstruction of initial
+ * pressure p0 and speed of sound c in 2-D photoacoustic tomography.
+ *
+ * The library computes, for K photoacoustic data sets that share one speed
+ * of sound map:
+ *   - the forward operator f^i : (p0^i, c) -> y^i of the observation model
+ *     y = f(x) + e (Sec. 2.2, Eq. ObservationModel), a k-space
+ *     pseudospectral solve of the acoustic initial value problem
+ *     (Sec. 2.1, Eq. WaveEquation) with a PML and point sensors;
+ *   - the data term of the objective (Eq. Minimised_functional) and its
+ *     exact discrete adjoint gradient with respect to every p0^i and c
+ *     (Sec. 3, Eqs. AdjointEquation, gradient_p0, gradient_sos);
+ *   - the projected L-BFGS reconstruction with backtracking (Eq.
+ *     BFGS_iterations, Algorithm 1, Eq. bound_constraints) over a
+ *     coarse-to-fine multigrid schedule (Sec. 3.1).
+ *
+ * Discretisation (the paper names the k-space method but does not restate
+ * it): first-order split-field staggered k-space leapfrog, wavenumbers
+ * k = 2 pi/(Ng dx) {-Ng/2 .. Ng/2-1}, correction kappa = sinc(c_ref |k| dt/2),
+ * staggering shifts exp(+-i k dx/2), PML alpha = pml_alpha (c_ref/dx)
+ * (depth/P)^4 applied as exp(-alpha dt/2) twice per update, uniform density
+ * rho0, p = c^2 (rho_x + rho_y), initial velocity u^{-1/2} = dt/(2 rho0) G p0.
+ *
+ * Conventions for every call:
+ *   - Fields are row-major [y][x] (x fastest), float32.  p0 and c cover the
+ *     N x N domain only; the PML (P cells per side) lies outside it and has
+ *     c = c_bg there.  Traces are [K][nt][m] (time-major).
+ *   - Pointers named d_* are DEVICE pointers owned by the caller; pointers
+ *     named h_* are host pointers.  Nothing returned to the caller is
+ *     allocated by the library; plans own their own small tables.
+ *   - Calls are asynchronous on the given CUDA stream (passed as void*, a
+ *     cudaStream_t; NULL = legacy default stream) unless stated.
+ *   - Return value: PAT_OK (0) or a negative PAT_E* code; pat_last_error()
+ *     gives a message for the calling thread.  Arguments are validated
+ *     before anything is launched.
+ */
+#ifndef PAT_H
+#define PAT_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PAT_OK 0
+#define PAT_EINVAL (-1)       /* bad shape, size, range or pointer */
+#define PAT_ENOMEM (-2)       /* workspace too small or allocation failed */
+#define PAT_ECUDA (-3)        /* a CUDA call failed */
+#define PAT_ENONFINITE (-4)   /* NaN/Inf met in the objective */
+#define PAT_ETIMEOUT (-5)     /* a bounded device wait gave up */
+#define PAT_ELINESEARCH (-6)  /* line search failed (reported, not fatal) */
+
+/* Discretisation of one grid level (Sec. 2.1; Table 1 style parameters).
+ * n: domain side N (cells), >= 2.  pml: PML width P (cells), >= 0; the FFT
+ * grid side Ng = n + 2 pml must be even, divisible by 4, 5-smooth
+ * (factors 2, 3, 5) and <= 1024.  dx: cell size (m).  dt: time step (s).
+ * nt: number of time samples t_n = n dt, n = 0..nt-1 (>= 1).  c_ref:
+ * reference speed of kappa and of the PML (the upper bound of c).  rho0:
+ * uniform density.  pml_alpha: PML strength (nepers per cell at the outer
+ * edge; 0 disables absorption).  c_bg: speed of sound outside the domain. */
+typedef struct {
+    int n;
+    int pml;
+    double dx;
+    double dt;
+    int nt;
+    double c_ref;
+    double rho0;
+    double pml_alpha;
+    double c_bg;
+} pat_grid;
+
+typedef struct pat_plan_s* pat_plan;
+
+/* Create a plan for K data sets with m point sensors (Sec. 4: point-like
+ * sensors; sampled by bilinear interpolation at their physical positions).
+ * h_sensor_xy: host [m][2] (x, y) in metres in the domain frame (origin at
+ * the lower-left corner of the domain, cell (iy, ix) centred at
+ * ((ix+0.5) dx, (iy+0.5) dx)); every sensor's 2x2 stencil must lie inside
+ * the FFT grid.  ckpt_every: wavefield checkpoint interval s used by the
+ * gradient (store the state every s steps, recompute in between); s >= nt
+ * stores the whole pressure history instead.  Tables (wavenumbers, kappa,
+ * PML, twiddles, sensor stencils) are computed in FP64 and stored in FP32
+ * on the current device.  *out receives the plan; destroy it with
+ * pat_plan_destroy (NULL is accepted). */
+int pat_plan_create(pat_plan* out, const pat_grid* grid, int m, const double* h_sensor_xy,
+                    int K, int ckpt_every);
+void pat_plan_destroy(pat_plan plan);
+
+/* FFT grid side Ng and PML width of a plan (for callers that size buffers). */
+int pat_plan_ng(pat_plan plan);
+
+/* Smallest PML width >= min_pml for which n + 2 P satisfies the grid rules
+ * above (Sec. 4.1.1: PML sized so the grid has small prime factors);
+ * returns -1 if none <= 1024 exists. */
+int pat_pml_auto(int n, int min_pml);
+
+/* Workspace sizes in bytes (caller allocates, 256-byte aligned device
+ * memory).  PAT_WS_FORWARD suffices for pat_forward; PAT_WS_GRADIENT holds
+ * the checkpoints and the adjoint state as well. */
+#define PAT_WS_FORWARD 0
+#define PAT_WS_GRADIENT 1
+size_t pat_workspace_bytes(pat_plan plan, int kind);
+
+/* Forward operator (Eq. ObservationModel without noise): d_y[k][n][m] =
+ * S p_k^n for the K initial pressures d_p0 [K][N][N] and the speed of sound
+ * d_c [N][N].  d_y [K][nt][m] is overwritten.  If ws_bytes >=
+ * pat_workspace_bytes(plan, PAT_WS_GRADIENT) the checkpoints needed by a
+ * following pat_vjp with the same c and p0 are kept in d_ws. */
+int pat_forward(pat_plan plan, const float* d_c, const float* d_p0, float* d_y,
+                void* d_ws, size_t ws_bytes, void* stream);
+
+/* Data term and its gradient (Eq. Minimised_functional without priors;
+ * Eqs. gradient_p0 and gradient_sos for the discrete scheme):
+ *   J = sum_k w_k/2 || y_pred_k - y_meas_k ||^2,
+ *   d_grad_p0 [K][N][N] = dJ/dp0_k,  d_grad_c [N][N] = dJ/dc summed over k.
+ * d_w: device [K] float weights w_k = 1/sigma_k^2 (L_e^T L_e = w_k I).
+ * d_J: device double (may be NULL) receives J.  d_y_pred: device
+ * [K][nt][m] (may be NULL) receives the predicted traces.  The workspace
+ * must hold PAT_WS_GRADIENT bytes.  Returns PAT_ENONFINITE only through
+ * *d_flag semantics of pat_status (the call itself stays asynchronous). */
+int pat_adjoint_grad(pat_plan plan, const float* d_c, const float* d_p0, const float* d_y_meas,
+                     const float* d_w, float* d_grad_p0, float* d_grad_c, double* d_J,
+                     float* d_y_pred, void* d_ws, size_t ws_bytes, void* stream);
+
+/* Vector-Jacobian product of the forward operator: given d_ybar [K][nt][m]
+ * (the adjoint source, e.g. dL/dy), returns d_grad_p0 = (df/dp0)^T ybar and
+ * d_grad_c = sum_k (df_k/dc)^T ybar_k.  Requires that the immediately
+ * preceding pat_forward on this plan and workspace used the same d_c and
+ * d_p0 with a PAT_WS_GRADIENT workspace (its checkpoints are reused). */
+int pat_vjp(pat_plan plan, const float* d_c, const float* d_p0, const float* d_ybar,
+            float* d_grad_p0, float* d_grad_c, void* d_ws, size_t ws_bytes, void* stream);
+
+/* Non-finite flag of the last objective evaluated on this workspace:
+ * copies it to *h_flag (1 if J or a residual was NaN/Inf) after
+ * synchronising the stream. */
+int pat_status(pat_plan plan, const void* d_ws, int* h_flag, void* stream);
+
+/* ---- reconstruction (Sec. 3, Sec. 3.1) ---- */
+
+/* Configuration of pat_reconstruct.  levels[nlevels]: domain sides N_l,
+ * coarse to fine, all covering the same physical side L (m), dx_l = L/N_l,
+ * dt_l = cfl dx_l / c_hi, nt_l = round(T/dt_l) + 1 with T = (nt_data-1)
+ * dt_data; PML >= min_pml cells per side.  Bounds: p0 >= p0_lo (no upper
+ * bound), c in [c_lo, c_hi] (Eq. bound_constraints); c_hi is also c_ref.
+ * mem: L-BFGS memory l (0 = projected Barzilai-Borwein gradient).  iters:
+ * iterations per level; a level also stops when the relative decrease of J
+ * is below rtol.  alpha0: first step in block-scaled units; c1: Armijo
+ * constant; max_halvings: backtracking halvings per line search; sigma_p0:
+ * block scale of p0 (c uses (c_hi - c_lo)/4).  ckpt_every: checkpoint
+ * interval of the gradient solves. */
+typedef struct {
+    int nlevels;
+    const int* levels;
+    double L;
+    double dt_data;
+    int nt_data;
+    int m;
+    const double* h_sensor_xy;
+    int K;
+    double cfl;
+    double c_lo, c_hi;
+    double p0_lo;
+    double c_bg;
+    double rho0;
+    double pml_alpha;
+    int min_pml;
+    int mem;
+    int iters;
+    int max_halvings;
+    int ckpt_every;
+    double rtol;
+    double alpha0;
+    double c1;
+    double sigma_p0;
+} pat_recon_cfg;
+
+/* One row per L-BFGS iteration. */
+typedef struct {
+    int level;
+    int iter;
+    double J;       /* objective before the step */
+    double gnorm;   /* ||g|| in block-scaled variables before the step */
+    double alpha;   /* accepted step (0 if the line search failed) */
+    int trials;     /* objective evaluations in the line search */
+    double J_new;   /* objective after the step */
+    double ms;      /* wall time of the iteration */
+} pat_iter_report;
+
+typedef struct {
+    int capacity;              /* rows available in iters (caller-owned host array) */
+    int count;                 /* rows written */
+    pat_iter_report* iters;
+    int status;                /* PAT_OK or PAT_ELINESEARCH if a level stopped on a failed search */
+    double total_ms;
+} pat_report;
+
+/* Joint reconstruction of p0_1..K and c (Sec. 3, 3.1).  d_y_meas: device
+ * [K][nt_data][m] data at t = n dt_data; d_w: device [K] weights.  d_c_io:
+ * device [N][N] on the finest level (N = levels[nlevels-1]); on input the
+ * initial guess (resampled bilinearly to the coarsest level), on output the
+ * reconstruction.  d_p0_io: device [K][N][N], same semantics.  The call
+ * synchronises the stream once per objective evaluation to read J (FP64
+ * line-search decisions on the host) and allocates its level buffers with
+ * stream-ordered allocation, freed before it returns. */
+int pat_reconstruct(const pat_recon_cfg* cfg, const float* d_y_meas, const float* d_w,
+                    float* d_c_io, float* d_p0_io, pat_report* report, void* stream);
+
+/* Message describing the last error on the calling thread. */
+const char* pat_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PAT_H */

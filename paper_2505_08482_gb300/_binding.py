@@ -1,0 +1,102 @@
+"""ctypes binding of ``libpat.so`` (argument marshalling only).
+
+Every entry point of ``include/pat.h`` is declared here under its C name.
+There is no fallback: if the library cannot be loaded the import of the
+product API fails loudly.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from ctypes import POINTER, c_char_p, c_double, c_int, c_size_t, c_void_p
+
+from ._build import LIB
+
+PAT_OK = 0
+PAT_EINVAL = -1
+PAT_ENOMEM = -2
+PAT_ECUDA = -3
+PAT_ENONFINITE = -4
+PAT_ETIMEOUT = -5
+PAT_ELINESEARCH = -6
+PAT_WS_FORWARD = 0
+PAT_WS_GRADIENT = 1
+
+
+class PatGrid(ctypes.Structure):
+    _fields_ = [("n", c_int), ("pml", c_int), ("dx", c_double), ("dt", c_double), ("nt", c_int),
+                ("c_ref", c_double), ("rho0", c_double), ("pml_alpha", c_double), ("c_bg", c_double)]
+
+
+class PatReconCfg(ctypes.Structure):
+    _fields_ = [("nlevels", c_int), ("levels", POINTER(c_int)), ("L", c_double), ("dt_data", c_double),
+                ("nt_data", c_int), ("m", c_int), ("h_sensor_xy", POINTER(c_double)), ("K", c_int),
+                ("cfl", c_double), ("c_lo", c_double), ("c_hi", c_double), ("p0_lo", c_double),
+                ("c_bg", c_double), ("rho0", c_double), ("pml_alpha", c_double), ("min_pml", c_int),
+                ("mem", c_int), ("iters", c_int), ("max_halvings", c_int), ("ckpt_every", c_int),
+                ("rtol", c_double), ("alpha0", c_double), ("c1", c_double), ("sigma_p0", c_double)]
+
+
+class PatIterReport(ctypes.Structure):
+    _fields_ = [("level", c_int), ("iter", c_int), ("J", c_double), ("gnorm", c_double), ("alpha", c_double),
+                ("trials", c_int), ("J_new", c_double), ("ms", c_double)]
+
+
+class PatReport(ctypes.Structure):
+    _fields_ = [("capacity", c_int), ("count", c_int), ("iters", POINTER(PatIterReport)), ("status", c_int),
+                ("total_ms", c_double)]
+
+
+# name -> (restype, argtypes)
+SIGNATURES = {
+    "pat_plan_create": (c_int, [POINTER(c_void_p), POINTER(PatGrid), c_int, POINTER(c_double), c_int, c_int]),
+    "pat_plan_destroy": (None, [c_void_p]),
+    "pat_plan_ng": (c_int, [c_void_p]),
+    "pat_pml_auto": (c_int, [c_int, c_int]),
+    "pat_workspace_bytes": (c_size_t, [c_void_p, c_int]),
+    "pat_forward": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),
+    "pat_adjoint_grad": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
+                                 c_void_p, c_void_p, c_size_t, c_void_p]),
+    "pat_vjp": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),
+    "pat_status": (c_int, [c_void_p, c_void_p, POINTER(c_int), c_void_p]),
+    "pat_reconstruct": (c_int, [POINTER(PatReconCfg), c_void_p, c_void_p, c_void_p, c_void_p, POINTER(PatReport),
+                                c_void_p]),
+    "pat_last_error": (c_char_p, []),
+}
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """Load libpat.so (built in-tree by ``build()``); raises if it is missing."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB):
+            raise RuntimeError(f"libpat.so not found at {LIB}: run paper_2505_08482_gb300.build() first")
+        try:
+            import torch  # noqa: F401  (loads the CUDA runtime first)
+        except ImportError:
+            pass
+        L = ctypes.CDLL(LIB)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def exported_symbols():
+    return list(SIGNATURES)
+
+
+class PatError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        msg = lib().pat_last_error()
+        super().__init__(f"{where} failed with code {code}: {msg.decode() if msg else ''}")
+        self.code = code
+
+
+def check(code: int, where: str):
+    if code != PAT_OK:
+        raise PatError(code, where)

@@ -1,0 +1,183 @@
+// C-ABI entry points of the forward operator and the adjoint gradient.
+//
+// Forward sweep (Sec. 2.1 scheme): init pass from p0, then Nt-1 steps of
+// four passes; with a gradient workspace the state (u^{n-1/2}, rho^n) is
+// copied every s steps and the pressure history of the last segment is kept.
+// Reverse sweep (Sec. 3 adjoint-state gradient, exact for the discrete
+// scheme): segments from last to first; each is recomputed from its
+// checkpoint (segment 0 from p0) while storing p^n, then the adjoint steps
+// run backwards through it, accumulating dJ/dc per data set; the n = 0
+// transposes of the initial condition close the sweep.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+
+#include "pat_internal.h"
+
+using namespace pat;
+
+namespace {
+
+#define RC(x)                   \
+    do {                        \
+        int rc_ = (x);          \
+        if (rc_ != PAT_OK) return rc_; \
+    } while (0)
+
+float scale_g(const pat_plan_s* p) {  // dt/rho0 G, inverse 2-D FFT normalisation folded in
+    return float(p->g.dt / p->g.rho0 / (double(p->ng) * p->ng));
+}
+float scale_d(const pat_plan_s* p) {  // dt rho0 D
+    return float(p->g.dt * p->g.rho0 / (double(p->ng) * p->ng));
+}
+
+// one forward step n -> n+1 given the row spectrum of p^n in A
+int step(const Launch& L, const Ws& w, int n, float* y, float* hist, int hist_slot) {
+    const pat_plan_s* p = L.p;
+    RC(launch_col(L, w.A, w.B, 0, 0, scale_g(p)));
+    RC(launch_row_u(L, w, n == 0));
+    RC(launch_col(L, w.A, w.B, 1, 1, scale_d(p)));
+    RC(launch_row_rho(L, w, 0, nullptr, y, n + 1, hist, hist_slot));
+    return PAT_OK;
+}
+
+size_t state_bytes(const pat_plan_s* p) { return 4 * size_t(p->K) * p->ng * p->ng * sizeof(float); }
+
+int forward_sweep(pat_plan_s* p, const float* c, const float* p0, float* y, const Ws& w, bool keep,
+                  cudaStream_t st) {
+    Launch L{p, st};
+    RC(launch_medium(L, c, w.cg));
+    PAT_CUDA(cudaMemsetAsync(y, 0, size_t(p->K) * p->nt * p->m * sizeof(float), st));
+    const int last0 = (p->nseg - 1) * p->s_eff;
+    RC(launch_row_rho(L, w, 1, p0, y, 0, (keep && last0 == 0) ? w.hist : nullptr, 0));
+    for (int n = 0; n + 1 < p->nt; ++n) {
+        if (keep && n > 0 && n % p->s_eff == 0) {
+            PAT_CUDA(cudaMemcpyAsync(w.ckpt + size_t(n / p->s_eff - 1) * 4 * p->K * p->ng * p->ng, w.ux,
+                                     state_bytes(p), cudaMemcpyDeviceToDevice, st));
+        }
+        const bool h = keep && (n + 1) >= last0;
+        RC(step(L, w, n, y, h ? w.hist : nullptr, n + 1 - last0));
+    }
+    return PAT_OK;
+}
+
+// reverse sweep with the weighted residual (or adjoint source) r [K][nt][m]
+int reverse_sweep(pat_plan_s* p, const float* p0, const float* r, float* grad_p0, float* grad_c, const Ws& w,
+                  bool hist_last_valid, cudaStream_t st) {
+    Launch L{p, st};
+    const size_t f = size_t(p->K) * p->ng * p->ng;
+    PAT_CUDA(cudaMemsetAsync(w.ubx, 0, 4 * f * sizeof(float), st));
+    PAT_CUDA(cudaMemsetAsync(w.cbar, 0, size_t(p->K) * p->n * p->n * sizeof(float), st));
+    const float sg = float(p->g.dt * p->g.rho0 / (double(p->ng) * p->ng));   // dt rho0 G t
+    const float sd = float(p->g.dt / p->g.rho0 / (double(p->ng) * p->ng));   // dt/rho0 D t'
+    bool have_q = false;
+    for (int j = p->nseg - 1; j >= 0; --j) {
+        const int n0 = j * p->s_eff;
+        const int n1 = std::min(n0 + p->s_eff, p->nt) - 1;
+        if (!(j == p->nseg - 1 && hist_last_valid)) {
+            // recompute the segment's pressure history
+            if (j == 0) {
+                RC(launch_row_rho(L, w, 1, p0, nullptr, 0, w.hist, 0));
+            } else {
+                PAT_CUDA(cudaMemcpyAsync(w.ux, w.ckpt + size_t(j - 1) * 4 * f, state_bytes(p),
+                                         cudaMemcpyDeviceToDevice, st));
+                RC(launch_row_rho(L, w, 2, nullptr, nullptr, 0, w.hist, 0));
+            }
+            for (int n = n0; n < n1; ++n) RC(step(L, w, n, nullptr, w.hist, n + 1 - n0));
+        }
+        for (int n = n1; n >= std::max(n0, 1); --n) {
+            RC(launch_row_adj_rho(L, w, have_q ? 0 : 1, r, n, w.hist, n - n0));
+            RC(launch_col(L, w.A2, w.B2, 1, 0, sg));
+            RC(launch_row_adj_u(L, w));
+            RC(launch_col(L, w.A2, w.B2, 2, 1, sd));
+            have_q = true;
+        }
+    }
+    RC(launch_row_adj_final1(L, w, have_q ? 0 : 1, r, grad_p0));
+    const float s0 = float(-0.5 * p->g.dt / p->g.rho0 / (double(p->ng) * p->ng));
+    RC(launch_col(L, w.A2, w.B2, 2, 1, s0));
+    RC(launch_row_adj_final2(L, w, p0, grad_p0));
+    RC(launch_reduce_cbar(L, w, grad_c));
+    return PAT_OK;
+}
+
+int check_ws(const pat_plan_s* p, const void* ws, size_t bytes, bool grad) {
+    if (!ws) { set_error("workspace is NULL"); return PAT_EINVAL; }
+    if (reinterpret_cast<uintptr_t>(ws) % 256 != 0) { set_error("workspace must be 256-byte aligned"); return PAT_EINVAL; }
+    const size_t need = grad ? p->ws_grad : p->ws_fwd;
+    if (bytes < need) {
+        set_error("workspace too small: %zu < %zu bytes", bytes, need);
+        return PAT_ENOMEM;
+    }
+    return PAT_OK;
+}
+
+}  // namespace
+
+int pat::objective(pat_plan_s* p, const float* c, const float* p0, const float* ymeas, const float* wts,
+                   double* J_dev, void* ws, size_t ws_bytes, cudaStream_t st) {
+    RC(check_ws(p, ws, ws_bytes, true));
+    Ws w = resolve(p, ws, true);
+    RC(forward_sweep(p, c, p0, w.ypred, w, false, st));
+    Launch L{p, st};
+    RC(launch_residual(L, w, w.ypred, ymeas, wts, w.resid, w.J));
+    if (J_dev) PAT_CUDA(cudaMemcpyAsync(J_dev, w.J, sizeof(double), cudaMemcpyDeviceToDevice, st));
+    p->hist_valid_ws = nullptr;
+    return PAT_OK;
+}
+
+extern "C" int pat_forward(pat_plan p, const float* c, const float* p0, float* y, void* ws, size_t ws_bytes,
+                           void* stream) {
+    if (!p || !c || !p0 || !y) { set_error("pat_forward: null argument"); return PAT_EINVAL; }
+    RC(check_ws(p, ws, ws_bytes, false));
+    const bool keep = ws_bytes >= p->ws_grad;
+    Ws w = resolve(p, ws, keep);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    RC(forward_sweep(p, c, p0, y, w, keep, st));
+    p->hist_valid_ws = keep ? ws : nullptr;
+    return PAT_OK;
+}
+
+extern "C" int pat_adjoint_grad(pat_plan p, const float* c, const float* p0, const float* y_meas, const float* wts,
+                                float* grad_p0, float* grad_c, double* J, float* y_pred, void* ws, size_t ws_bytes,
+                                void* stream) {
+    if (!p || !c || !p0 || !y_meas || !wts || !grad_p0 || !grad_c) {
+        set_error("pat_adjoint_grad: null argument");
+        return PAT_EINVAL;
+    }
+    RC(check_ws(p, ws, ws_bytes, true));
+    Ws w = resolve(p, ws, true);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    float* yp = y_pred ? y_pred : w.ypred;
+    RC(forward_sweep(p, c, p0, yp, w, true, st));
+    Launch L{p, st};
+    RC(launch_residual(L, w, yp, y_meas, wts, w.resid, w.J));
+    if (J) PAT_CUDA(cudaMemcpyAsync(J, w.J, sizeof(double), cudaMemcpyDeviceToDevice, st));
+    RC(reverse_sweep(p, p0, w.resid, grad_p0, grad_c, w, true, st));
+    p->hist_valid_ws = nullptr;
+    return PAT_OK;
+}
+
+extern "C" int pat_vjp(pat_plan p, const float* c, const float* p0, const float* ybar, float* grad_p0, float* grad_c,
+                       void* ws, size_t ws_bytes, void* stream) {
+    if (!p || !c || !p0 || !ybar || !grad_p0 || !grad_c) { set_error("pat_vjp: null argument"); return PAT_EINVAL; }
+    RC(check_ws(p, ws, ws_bytes, true));
+    Ws w = resolve(p, ws, true);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    Launch L{p, st};
+    RC(launch_medium(L, c, w.cg));
+    const bool valid = (p->hist_valid_ws == ws);
+    RC(reverse_sweep(p, p0, ybar, grad_p0, grad_c, w, valid, st));
+    p->hist_valid_ws = nullptr;
+    return PAT_OK;
+}
+
+extern "C" int pat_status(pat_plan p, const void* ws, int* h_flag, void* stream) {
+    if (!p || !ws || !h_flag) { set_error("pat_status: null argument"); return PAT_EINVAL; }
+    const char* b = static_cast<const char*>(ws);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    PAT_CUDA(cudaMemcpyAsync(h_flag, b + p->o_flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+    PAT_CUDA(cudaStreamSynchronize(st));
+    return PAT_OK;
+}

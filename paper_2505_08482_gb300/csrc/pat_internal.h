@@ -1,0 +1,113 @@
+// Internal declarations of the k-space solver library: plan, workspace
+// layout and kernel launchers.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <string>
+
+#include "../../include/pat.h"
+#include "fft.cuh"
+
+namespace pat {
+
+void set_error(const char* fmt, ...);
+int cuda_fail(cudaError_t e, const char* where);
+
+#define PAT_CUDA(call)                                           \
+    do {                                                         \
+        cudaError_t e_ = (call);                                 \
+        if (e_ != cudaSuccess) return ::pat::cuda_fail(e_, #call); \
+    } while (0)
+
+// Device tables of one plan (all built in FP64 on the host, stored FP32).
+struct Tables {
+    float2* tw;        // [ng] exp(-2 pi i q / ng)
+    float* kappa_t;    // [hc][ng] kappa(kx, ky) at kx * ng + ky
+    float2* fx;        // [hc] i kx exp(+i kx dx/2)   (x factor of G; D uses -conj)
+    float2* fy;        // [ng] i ky exp(+i ky dx/2)   (y factor of G; D uses -conj)
+    float* a_cell;     // [ng] PML factor at cell centres
+    float* a_stag;     // [ng] PML factor at +1/2 cell
+    int* srow;         // [ng+1] CSR row pointer of sensor stencil entries
+    int2* sent;        // [nent] (sensor m, column ix) per entry
+    float4* sentw;     // [nent] (w_x0, w_x1, w_y, row) per entry
+};
+
+// Workspace regions (device pointers resolved from the caller's base).
+struct Ws {
+    float* ux; float* uy; float* rx; float* ry;   // forward state [K][ng][ng] each (contiguous)
+    float* cg;                                    // c on the grid [ng][ng]
+    float2* A; float2* B;                         // spectra [K][ng][hc]
+    double* J; double* part; int* flag;           // objective, partial sums, non-finite flag
+    // gradient only
+    float* ckpt;                                  // [nseg-1][4][K][ng][ng]
+    float* hist;                                  // [K][s_eff][ng][ng] pressure history
+    float* ubx; float* uby; float* rbx; float* rby;  // adjoint state [K][ng][ng]
+    float2* A2; float2* B2;                       // adjoint spectra
+    float* cbar;                                  // [K][n][n]
+    float* resid;                                 // [K][nt][m]
+    float* ypred;                                 // [K][nt][m]
+};
+
+constexpr int kPartials = 256;
+
+}  // namespace pat
+
+struct pat_plan_s {
+    pat_grid g;
+    int n, P, ng, hc, K, nt, m, s, s_eff, nseg;
+    pat::FftDesc fft;
+    int R;             // rows per CTA in row passes (even)
+    int C;             // spectral columns per CTA in column passes
+    size_t smem_row, smem_col;
+    void* dev;         // one device allocation for the tables
+    pat::Tables t;
+    int nent;
+    size_t ws_fwd, ws_grad;
+    // layout offsets (bytes)
+    size_t o_state, o_cg, o_A, o_B, o_J, o_part, o_flag;
+    size_t o_ckpt, o_hist, o_adj, o_A2, o_B2, o_cbar, o_resid, o_ypred;
+    // host bookkeeping: the workspace whose history holds the last segment
+    const void* hist_valid_ws;
+    int device;
+};
+
+namespace pat {
+
+Ws resolve(const pat_plan_s* p, void* base, bool grad);
+
+// ---- kernel launchers (kernels.cu) ----
+struct Launch {
+    const pat_plan_s* p;
+    cudaStream_t st;
+};
+
+int configure_kernels(pat_plan_s* p);
+
+// forward
+int launch_medium(const Launch& L, const float* c_dom, float* cg);
+// row pass producing rho and p (mode 0 regular, 1 init from p0, 2 restore)
+int launch_row_rho(const Launch& L, const Ws& w, int mode, const float* p0, float* y, int tstep,
+                   float* hist, int hist_slot);
+int launch_row_u(const Launch& L, const Ws& w, int init);
+// column passes: mode 0 = one input (A) -> (MX A, MY A) into (A, B)
+//                mode 1 = (A, B) -> (MX A, MY B); mode 2 = (A, B) -> MX A + MY B into A
+// op 0: G multipliers, op 1: D multipliers
+int launch_col(const Launch& L, float2* A, float2* B, int mode, int op, float scale);
+// adjoint
+int launch_row_adj_rho(const Launch& L, const Ws& w, int first, const float* resid, int tstep,
+                       const float* hist, int hist_slot);
+int launch_row_adj_u(const Launch& L, const Ws& w);
+int launch_row_adj_final1(const Launch& L, const Ws& w, int first, const float* resid, float* grad_p0);
+int launch_row_adj_final2(const Launch& L, const Ws& w, const float* p0, float* grad_p0);
+int launch_reduce_cbar(const Launch& L, const Ws& w, float* grad_c);
+int launch_residual(const Launch& L, const Ws& w, const float* ypred, const float* ymeas,
+                    const float* wts, float* resid, double* J_out);
+
+// ---- api.cu internals used by the reconstruction driver ----
+// J only (forward sweep + residual) into *J_dev; workspace of PAT_WS_GRADIENT size.
+int objective(pat_plan_s* p, const float* c, const float* p0, const float* ymeas, const float* wts, double* J_dev,
+              void* ws, size_t ws_bytes, cudaStream_t st);
+
+}  // namespace pat

@@ -1,0 +1,168 @@
+"""Torch-facing wrapper of the C ABI: plans, workspaces, forward and gradient.
+
+Device memory and streams come from PyTorch; every computation runs in the
+CUDA kernels of ``libpat.so`` (there is no CPU or PyTorch fallback).
+"""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+from . import _binding as B
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _f32(t, shape, name, device):
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a torch tensor")
+    if t.dtype != torch.float32 or not t.is_cuda or not t.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous float32 CUDA tensor")
+    if tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} has shape {tuple(t.shape)}, expected {tuple(shape)}")
+    if t.device != device:
+        raise ValueError(f"{name} is on {t.device}, plan is on {device}")
+    return t
+
+
+def pml_auto(n: int, min_pml: int = 20) -> int:
+    """Smallest PML width >= min_pml giving a valid FFT grid (library rule)."""
+    return int(B.lib().pat_pml_auto(int(n), int(min_pml)))
+
+
+@dataclass
+class GridSpec:
+    n: int
+    pml: int
+    dx: float
+    dt: float
+    nt: int
+    c_ref: float
+    rho0: float = 1000.0
+    pml_alpha: float = 2.0
+    c_bg: float = 1500.0
+
+    @property
+    def ng(self):
+        return self.n + 2 * self.pml
+
+
+class Plan:
+    """A solver plan for K data sets on one grid (wraps pat_plan)."""
+
+    def __init__(self, grid: GridSpec, sensors_xy, K: int, ckpt_every: int = 32, device=None):
+        self.grid = grid
+        self.K = int(K)
+        self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        xy = np.ascontiguousarray(np.asarray(sensors_xy, dtype=np.float64))
+        if xy.ndim != 2 or xy.shape[1] != 2:
+            raise ValueError("sensors_xy must be [M][2]")
+        self.m = xy.shape[0]
+        self.nt = grid.nt
+        self.n = grid.n
+        g = B.PatGrid(grid.n, grid.pml, grid.dx, grid.dt, grid.nt, grid.c_ref, grid.rho0, grid.pml_alpha, grid.c_bg)
+        h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            B.check(B.lib().pat_plan_create(ctypes.byref(h), ctypes.byref(g), self.m,
+                                            xy.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), self.K,
+                                            int(ckpt_every)), "pat_plan_create")
+        self._h = h
+        self.ckpt_every = int(ckpt_every)
+        self._ws = {}
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            try:
+                B.lib().pat_plan_destroy(h)
+            except Exception:
+                pass
+            self._h = None
+
+    @property
+    def ng(self):
+        return int(B.lib().pat_plan_ng(self._h))
+
+    def workspace_bytes(self, kind: int = B.PAT_WS_GRADIENT) -> int:
+        return int(B.lib().pat_workspace_bytes(self._h, kind))
+
+    def workspace(self, kind: int = B.PAT_WS_GRADIENT):
+        """Cached device workspace (torch uint8 tensor, 512-byte aligned)."""
+        ws = self._ws.get(kind)
+        if ws is None:
+            ws = torch.empty(max(self.workspace_bytes(kind), 256), dtype=torch.uint8, device=self.device)
+            self._ws[kind] = ws
+        return ws
+
+    def _shapes(self):
+        n, K = self.n, self.K
+        return (n, n), (K, n, n), (K, self.nt, self.m)
+
+    def forward(self, c, p0, y=None, keep_checkpoints=False, stream=None, ws=None):
+        """Sensor traces y [K][nt][m] (pat_forward)."""
+        sc, sp, sy = self._shapes()
+        _f32(c, sc, "c", self.device)
+        _f32(p0, sp, "p0", self.device)
+        if y is None:
+            y = torch.empty(sy, dtype=torch.float32, device=self.device)
+        _f32(y, sy, "y", self.device)
+        kind = B.PAT_WS_GRADIENT if keep_checkpoints else B.PAT_WS_FORWARD
+        if ws is None:
+            ws = self.workspace(kind)
+        B.check(B.lib().pat_forward(self._h, _ptr(c), _ptr(p0), _ptr(y), _ptr(ws), self.workspace_bytes(kind),
+                                    _stream(stream)), "pat_forward")
+        return y
+
+    def adjoint_grad(self, c, p0, y_meas, w, grad_p0=None, grad_c=None, J=None, y_pred=None, stream=None, ws=None):
+        """(J [device float64 scalar], dJ/dp0 [K][n][n], dJ/dc [n][n]) (pat_adjoint_grad)."""
+        sc, sp, sy = self._shapes()
+        _f32(c, sc, "c", self.device)
+        _f32(p0, sp, "p0", self.device)
+        _f32(y_meas, sy, "y_meas", self.device)
+        _f32(w, (self.K,), "w", self.device)
+        if grad_p0 is None:
+            grad_p0 = torch.empty(sp, dtype=torch.float32, device=self.device)
+        if grad_c is None:
+            grad_c = torch.empty(sc, dtype=torch.float32, device=self.device)
+        if J is None:
+            J = torch.empty((), dtype=torch.float64, device=self.device)
+        if y_pred is not None:
+            _f32(y_pred, sy, "y_pred", self.device)
+        if ws is None:
+            ws = self.workspace(B.PAT_WS_GRADIENT)
+        B.check(B.lib().pat_adjoint_grad(self._h, _ptr(c), _ptr(p0), _ptr(y_meas), _ptr(w), _ptr(grad_p0),
+                                         _ptr(grad_c), _ptr(J), _ptr(y_pred), _ptr(ws),
+                                         self.workspace_bytes(B.PAT_WS_GRADIENT), _stream(stream)),
+                "pat_adjoint_grad")
+        return J, grad_p0, grad_c
+
+    def vjp(self, c, p0, ybar, stream=None, ws=None):
+        """(df/dp0)^T ybar and sum_k (df_k/dc)^T ybar_k (pat_vjp)."""
+        sc, sp, sy = self._shapes()
+        _f32(c, sc, "c", self.device)
+        _f32(p0, sp, "p0", self.device)
+        _f32(ybar, sy, "ybar", self.device)
+        gp = torch.empty(sp, dtype=torch.float32, device=self.device)
+        gc = torch.empty(sc, dtype=torch.float32, device=self.device)
+        if ws is None:
+            ws = self.workspace(B.PAT_WS_GRADIENT)
+        B.check(B.lib().pat_vjp(self._h, _ptr(c), _ptr(p0), _ptr(ybar), _ptr(gp), _ptr(gc), _ptr(ws),
+                                self.workspace_bytes(B.PAT_WS_GRADIENT), _stream(stream)), "pat_vjp")
+        return gp, gc
+
+    def nonfinite(self, stream=None) -> bool:
+        """True if the last objective on the gradient workspace met NaN/Inf (synchronises)."""
+        flag = ctypes.c_int(0)
+        ws = self.workspace(B.PAT_WS_GRADIENT)
+        B.check(B.lib().pat_status(self._h, _ptr(ws), ctypes.byref(flag), _stream(stream)), "pat_status")
+        return bool(flag.value)
