@@ -1,0 +1,421 @@
+#!/usr/bin/env python
+"""Benchmark of the joint p0 / speed-of-sound reconstruction hot path on GB300.
+
+Headline: gradient evaluations per second (one step = one call of
+pat_adjoint_grad: forward solve with checkpoints every s = 32 steps, residual
+and objective, segment recompute and time-reversed adjoint accumulating
+dJ/dp0_k and dJ/dc over the K data sets) on the 256 x 256 domain (300 x 300
+FFT grid with a 22-cell PML), K = 8 vessel-like p0 sets, 512 sensors on a
+circle, Nt = 1800, FP32.  Inputs are seeded synthetic stand-ins for the
+paper's phantoms (pat_synth).
+
+Also reported: forward-only Gcell-steps/s (Ng^2 K (Nt-1) / s), an
+end-to-end number through host buffers (H2D of c, p0, data, weights and D2H
+of both gradients and J inside the timed region), the roofline of the
+dominant kernel (algorithmic bytes per launch / average launch time from
+CUDA events on the launching stream), SM clocks sampled during the timed
+region and the FP64 oracle timed on the host cores on a bounded sample.
+
+``--impl reference`` times the FP64 oracle (the only reference: the paper
+ships no code) on the same workload, on bounded samples scaled to the metric.
+
+Multi-GPU (torchrun): every rank solves its own independent problem (weak
+scaling, replicas: the path needs no collective on one box); rank 0 prints.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "grad evals/s & Gcell-steps/s at 256²×K=8; time-to-rel.err vs plain GPU"
+UNIT = "grad evals/s"
+WL = dict(workload="vessels256", n=256, K=8, M=512, nt=1800, ckpt_every=32, dx=1e-4, c_lo=1350.0, c_hi=1750.0,
+          cfl=0.3, pml_alpha=2.0, c_bg=1500.0)
+
+# Algorithmic bytes per grid cell (Ng^2 cells per data set) and launch, FP32.
+# A spectrum row holds Ng/2+1 complex values: 8 (Ng/2+1)/Ng bytes per cell.
+def bytes_per_cell(cls: int, ng: int, n: int, ckpt_hist: bool = True) -> float:
+    spec = 8.0 * (ng // 2 + 1) / ng
+    dom = (n * n) / float(ng * ng)
+    table = {
+        1: 2 * spec + 8 + 4 + 8 + spec + (4 if ckpt_hist else 0),   # row_rho: 2 spectra, rho r+w, c, p spectrum, hist
+        2: 2 * spec + 8 + 8 + 2 * spec,                              # row_u: 2 spectra in, u r+w, 2 spectra out
+        3: spec + 2 * spec,                                          # col grad: 1 in, 2 out
+        4: 2 * spec + 2 * spec,                                      # col pair: 2 in, 2 out
+        5: 2 * spec + spec,                                          # col sum: 2 in, 1 out
+        6: spec + 8 + 4 + 4 + 8 * dom + 8 + 2 * spec,                # adj rho: spectrum, rb r+w, c, hist, cbar r+w, 2 out
+        7: 2 * spec + 8 + 8 + 2 * spec,                              # adj u
+    }
+    return table[cls]
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2505_08482_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh", ".h")):
+            h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--ckpt", type=int, default=WL["ckpt_every"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample-steps", type=int, default=0, help="oracle sample length (0 = auto)")
+    return ap.parse_args()
+
+
+def inputs(seed: int):
+    import numpy as np
+    import pat_synth as ps
+    w = ps.workload(WL["workload"], seed)
+    c_init = 0.5 * (w.c_true.min() + w.c_true.max())
+    return w, c_init
+
+
+def pml_auto(n, min_pml=20):
+    from paper_2505_08482_gb300.solver import pml_auto as pa
+    return pa(n, min_pml)
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason sampling during the timed region."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,utilization.gpu,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append(dict(sm=float(parts[0]), smax=float(parts[1]), util=float(parts[3]),
+                                 hw=parts[5], hwt=parts[6], swt=parts[7], pcap=parts[8]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        load = [r for r in rows if r["util"] >= 50] or rows
+        reasons = set()
+        for r in load:
+            for key, name in (("hw", "hw_slowdown"), ("hwt", "hw_thermal_slowdown"),
+                              ("swt", "sw_thermal_slowdown"), ("pcap", "sw_power_cap")):
+                if r[key].lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(r["sm"] for r in load), "sm_max_mhz": max(r["smax"] for r in rows),
+                "reasons": sorted(reasons), "samples": len(load)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def stored_traffic(cls: int, src_hash: str):
+    """Per-launch DRAM bytes of kernel class cls from the committed ncu summary, if current."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    e = d.get(str(cls))
+    if not e or d.get("kernel_source_hash") != src_hash:
+        return None
+    return e.get("dram_bytes_per_launch_full")
+
+
+# ---------------------------------------------------------------------------
+def oracle_sample(seed: int, nt_s: int, K_s: int = 1):
+    """One oracle gradient on a bounded sample of the workload; returns seconds."""
+    import numpy as np
+    import pat_synth as ps
+    from oracle.adjoint import adjoint_grad
+    from oracle.grid import make_grid
+    from oracle.sensors import sensor_matrix
+    w, c_init = inputs(seed)
+    g = make_grid(w.n, w.dx, nt_s, c_ref=WL["c_hi"], cfl=WL["cfl"])
+    S = sensor_matrix(g, w.sensors)
+    rng = ps.rng_for(1000 + seed)
+    ym = rng.standard_normal((K_s, nt_s, w.m)) * 0.01
+    p0 = 0.5 * w.p0_true[:K_s]
+    c0 = np.full((w.n, w.n), c_init)
+    t = time.perf_counter()
+    adjoint_grad(g, c0, p0, S, ym, np.ones(K_s))
+    return time.perf_counter() - t
+
+
+def cpu_value(seconds: float, nt_s: int, K_s: int) -> float:
+    """Oracle grad evals/s scaled from a sample (cost is linear in K and in Nt)."""
+    scale = (WL["K"] * (WL["nt"] - 1)) / float(K_s * (nt_s - 1))
+    return 1.0 / (seconds * scale)
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return
+    nt_s = args.cpu_sample_steps or 300
+    for _ in range(args.warmup):
+        oracle_sample(0, nt_s)
+    ts = [oracle_sample(0, nt_s) for _ in range(args.steps)]
+    t = sum(ts) / len(ts)
+    v = cpu_value(t, nt_s, 1)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 / v, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": cfg_dict(args),
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"one FP64 oracle gradient at K=1, Nt={nt_s} on the same 300^2 grid per "
+                                       f"step, scaled by K*(Nt-1) to K=8, Nt=1800"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def cfg_dict(args):
+    return {"workload": f"{WL['workload']}: 256x256 domain (Ng 300, PML 22), K=8 vessel p0 sets, "
+                        f"M=512 circle sensors, Nt=1800, s={args.ckpt}, 6 c inclusions",
+            "global_batch": WL["K"] * args.gpus, "n": WL["n"], "K": WL["K"], "M": WL["M"], "nt": WL["nt"],
+            "ckpt_every": args.ckpt, "parallelism": f"replicas x{args.gpus}",
+            "l2": "256 MiB buffer written between timed steps (working set of one step is L2-resident)"}
+
+
+def run_ours(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+
+    import pat_synth as ps
+    import paper_2505_08482_gb300 as pkg
+    from paper_2505_08482_gb300 import _binding as B
+    from paper_2505_08482_gb300.solver import GridSpec, Plan
+
+    pkg.build()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    L = B.lib()
+    w, c_init = inputs(rank)
+    n, K, M, nt = WL["n"], WL["K"], WL["M"], WL["nt"]
+    P = pml_auto(n)
+    dt = WL["cfl"] * WL["dx"] / WL["c_hi"]
+    gs = GridSpec(n=n, pml=P, dx=WL["dx"], dt=dt, nt=nt, c_ref=WL["c_hi"], pml_alpha=WL["pml_alpha"],
+                  c_bg=WL["c_bg"])
+    ng = gs.ng
+    plan = Plan(gs, w.sensors, K, ckpt_every=args.ckpt, device=dev)
+    f32 = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float32, device=dev)
+    c_true, p0_true = f32(w.c_true), f32(w.p0_true)
+    y_clean = plan.forward(c_true, p0_true).cpu().numpy()
+    ym_np = ps.add_noise(y_clean, ps.rng_for(500 + rank))
+    w_np = ps.noise_weights(ym_np)
+    ym, wt = f32(ym_np), f32(w_np)
+    c0 = f32(np.full((n, n), c_init))
+    p0 = f32(0.5 * w.p0_true)
+    gp0 = torch.empty((K, n, n), dtype=torch.float32, device=dev)
+    gc = torch.empty((n, n), dtype=torch.float32, device=dev)
+    J = torch.empty((), dtype=torch.float64, device=dev)
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
+
+    def grad_eval():
+        plan.adjoint_grad(c0, p0, ym, wt, grad_p0=gp0, grad_c=gc, J=J)
+
+    for _ in range(args.warmup):
+        grad_eval()
+    torch.cuda.synchronize()
+    # per-class kernel time of one evaluation (outside the timed region) -> dominant kernel
+    per_class = {}
+    for cls in B.KERNEL_CLASSES:
+        B.check(L.pat_timing_enable(cls, 8000), "pat_timing_enable")
+        grad_eval()
+        tot, cnt = ctypes_read(L)
+        per_class[cls] = (tot, cnt)
+    B.check(L.pat_timing_enable(0, 0), "pat_timing_enable")
+    dom = max(per_class, key=lambda c: per_class[c][0])
+    per_eval_launches = per_class[dom][1]
+    B.check(L.pat_timing_enable(dom, per_eval_launches * args.steps + 16), "pat_timing_enable")
+
+    dist = world > 1
+    if dist:
+        import torch.distributed as tdist
+    sampler = ClockSampler(local_rank)
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    launches0 = L.pat_kernel_launches()
+    sampler.start()
+    if dist:
+        tdist.barrier()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.steps):
+        flush.zero_()
+        grad_eval()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        tdist.barrier()
+    clocks = sampler.stop()
+    launches = int(L.pat_kernel_launches() - launches0)
+    t_ms = e0.elapsed_time(e1)
+    dom_ms, dom_cnt = ctypes_read(L)
+    B.check(L.pat_timing_enable(0, 0), "pat_timing_enable")
+    if dist:
+        tt = torch.tensor([t_ms], dtype=torch.float64, device=dev)
+        tdist.all_reduce(tt, op=tdist.ReduceOp.MAX)
+        t_ms = float(tt.item())
+    value = world * args.steps / (t_ms / 1000.0)
+
+    # forward-only throughput (Gcell-steps/s) on the same workload
+    yb = torch.empty((K, nt, M), dtype=torch.float32, device=dev)
+    for _ in range(2):
+        plan.forward(c0, p0, y=yb)
+    torch.cuda.synchronize()
+    nf = max(2, args.steps)
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    for _ in range(nf):
+        flush.zero_()
+        plan.forward(c0, p0, y=yb)
+    f1.record(stream)
+    torch.cuda.synchronize()
+    fwd_s = f0.elapsed_time(f1) / 1000.0 / nf
+    gcell = ng * ng * K * (nt - 1) / fwd_s / 1e9
+
+    # end to end through host buffers (pinned), the call a user makes
+    pin = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float32).pin_memory()
+    h_c, h_p0, h_ym, h_w = pin(np.full((n, n), c_init)), pin(0.5 * w.p0_true), pin(ym_np), pin(w_np)
+    h_gp0 = torch.empty((K, n, n), dtype=torch.float32).pin_memory()
+    h_gc = torch.empty((n, n), dtype=torch.float32).pin_memory()
+    h_J = torch.empty((), dtype=torch.float64).pin_memory()
+    d_c, d_p0, d_ym, d_w = (torch.empty_like(t, device=dev) for t in (h_c, h_p0, h_ym, h_w))
+    h2d = sum(t.numel() * t.element_size() for t in (h_c, h_p0, h_ym, h_w))
+    d2h = sum(t.numel() * t.element_size() for t in (h_gp0, h_gc, h_J))
+
+    def e2e_step():
+        for d, h in ((d_c, h_c), (d_p0, h_p0), (d_ym, h_ym), (d_w, h_w)):
+            d.copy_(h, non_blocking=True)
+        plan.adjoint_grad(d_c, d_p0, d_ym, d_w, grad_p0=gp0, grad_c=gc, J=J)
+        h_gp0.copy_(gp0, non_blocking=True)
+        h_gc.copy_(gc, non_blocking=True)
+        h_J.copy_(J, non_blocking=True)
+
+    e2e_step()
+    torch.cuda.synchronize()
+    g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if dist:
+        tdist.barrier()
+    g0.record(stream)
+    for _ in range(args.steps):
+        flush.zero_()
+        e2e_step()
+    g1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = g0.elapsed_time(g1)
+    if dist:
+        tt = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
+        tdist.all_reduce(tt, op=tdist.ReduceOp.MAX)
+        e2e_ms = float(tt.item())
+    e2e_val = world * args.steps / (e2e_ms / 1000.0)
+
+    # roofline of the dominant kernel
+    peak, peak_kind = measured_peaks()
+    bpl = bytes_per_cell(dom, ng, n) * ng * ng * K
+    avg_s = dom_ms / 1000.0 / max(dom_cnt, 1)
+    achieved = bpl / avg_s / 1e9
+    src_hash = kernel_source_hash()
+    roof = {"bound": "hbm", "kernel": B.KERNEL_CLASSES[dom], "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "traffic": stored_traffic(dom, src_hash),
+            "peak_kind": f"{peak_kind} hbm_gbs", "algorithmic_bytes_per_launch": bpl,
+            "avg_launch_us": avg_s * 1e6, "launches_timed": dom_cnt,
+            "share_of_step": dom_ms / t_ms if t_ms > 0 else None,
+            "per_class_ms_per_eval": {B.KERNEL_CLASSES[c]: round(v[0], 3) for c, v in per_class.items()}}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": cfg_dict(args),
+            "forward_gcell_steps_per_s": gcell * world, "forward_ms": fwd_s * 1000.0,
+            "grad_gcell_steps_per_s": value * ng * ng * K * (nt - 1) / 1e9,
+            "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": launches, "roofline": roof, "clocks": clocks, "kernel_source_hash": src_hash}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        nt_s = args.cpu_sample_steps or 300
+        ts = oracle_sample(0, nt_s)
+        v = cpu_value(ts, nt_s, 1)
+        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": f"one FP64 oracle gradient at K=1, Nt={nt_s} on the same 300^2 grid "
+                                          f"({ts:.1f} s), scaled by K*(Nt-1) to K=8, Nt=1800"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def ctypes_read(L):
+    import ctypes
+    tot = ctypes.c_double(0.0)
+    cnt = ctypes.c_longlong(0)
+    rc = L.pat_timing_read(ctypes.byref(tot), ctypes.byref(cnt))
+    if rc != 0:
+        raise RuntimeError("pat_timing_read failed")
+    return tot.value, cnt.value
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as tdist
+        torch.cuda.set_device(local_rank)
+        tdist.init_process_group("nccl")
+    run_ours(args, rank, world, local_rank)
+    if world > 1:
+        import torch.distributed as tdist
+        tdist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -54,8 +54,8 @@ extern "C" {
 
 /* Discretisation of one grid level (Sec. 2.1; Table 1 style parameters).
  * n: domain side N (cells), >= 2.  pml: PML width P (cells), >= 0; the FFT
- * grid side Ng = n + 2 pml must be even, divisible by 4, 5-smooth
- * (factors 2, 3, 5) and <= 1024.  dx: cell size (m).  dt: time step (s).
+ * grid side Ng = n + 2 pml must be even, 5-smooth (factors 2, 3, 5) and
+ * <= 1024.  dx: cell size (m).  dt: time step (s).
  * nt: number of time samples t_n = n dt, n = 0..nt-1 (>= 1).  c_ref:
  * reference speed of kappa and of the PML (the upper bound of c).  rho0:
  * uniform density.  pml_alpha: PML strength (nepers per cell at the outer
@@ -207,6 +207,30 @@ typedef struct {
  * stream-ordered allocation, freed before it returns. */
 int pat_reconstruct(const pat_recon_cfg* cfg, const float* d_y_meas, const float* d_w,
                     float* d_c_io, float* d_p0_io, pat_report* report, void* stream);
+
+/* ---- instrumentation (benchmarking; not thread-safe) ---- */
+
+/* Kernel classes that can be timed. */
+#define PAT_K_ROW_RHO 1       /* forward density / pressure row pass (incl. sensor gather) */
+#define PAT_K_ROW_U 2         /* forward velocity row pass */
+#define PAT_K_COL_GRAD 3      /* column pass, one spectrum in, two out (forward G) */
+#define PAT_K_COL_PAIR 4      /* column pass, two in, two out (forward D, adjoint G) */
+#define PAT_K_COL_SUM 5       /* column pass, two in, one out (adjoint D) */
+#define PAT_K_ROW_ADJ_RHO 6   /* adjoint density row pass (incl. scatter, dJ/dc) */
+#define PAT_K_ROW_ADJ_U 7     /* adjoint velocity row pass */
+#define PAT_K_LAST 7
+
+/* Total number of kernels this library has launched in the process. */
+unsigned long long pat_kernel_launches(void);
+
+/* Record a pair of CUDA events on the launching stream around each of the
+ * next max_launches launches of kernel class cls (0 disables).  Events are
+ * created here, outside any timed region. */
+int pat_timing_enable(int cls, int max_launches);
+
+/* Sum of the recorded launch durations (ms) and their count; waits for the
+ * last recorded event and resets the counter. */
+int pat_timing_read(double* total_ms, long long* launches);
 
 /* Message describing the last error on the calling thread. */
 const char* pat_last_error(void);

@@ -38,7 +38,12 @@ def is_smooth(n: int, primes=(2, 3, 5)) -> bool:
 
 
 def pml_auto(n: int, min_pml: int = 20) -> int:
-    """Smallest PML width P >= min_pml with N + 2P even and 5-smooth (Sec. 4.1.1)."""
+    """Smallest PML width P >= min_pml with N + 2P even and 5-smooth (Sec. 4.1.1).
+
+    An odd N has no even grid side; that raises ValueError.
+    """
+    if n % 2:
+        raise ValueError("an odd domain side has no even FFT grid side")
     p = min_pml
     while not ((n + 2 * p) % 2 == 0 and is_smooth(n + 2 * p)):
         p += 1

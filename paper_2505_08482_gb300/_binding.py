@@ -19,6 +19,15 @@ PAT_ECUDA = -3
 PAT_ENONFINITE = -4
 PAT_ETIMEOUT = -5
 PAT_ELINESEARCH = -6
+PAT_K_ROW_RHO = 1
+PAT_K_ROW_U = 2
+PAT_K_COL_GRAD = 3
+PAT_K_COL_PAIR = 4
+PAT_K_COL_SUM = 5
+PAT_K_ROW_ADJ_RHO = 6
+PAT_K_ROW_ADJ_U = 7
+KERNEL_CLASSES = {1: "k_row_rho", 2: "k_row_u", 3: "k_col(grad)", 4: "k_col(pair)", 5: "k_col(sum)",
+                  6: "k_row_adj_rho", 7: "k_row_adj_u"}
 PAT_WS_FORWARD = 0
 PAT_WS_GRADIENT = 1
 
@@ -61,6 +70,9 @@ SIGNATURES = {
     "pat_status": (c_int, [c_void_p, c_void_p, POINTER(c_int), c_void_p]),
     "pat_reconstruct": (c_int, [POINTER(PatReconCfg), c_void_p, c_void_p, c_void_p, c_void_p, POINTER(PatReport),
                                 c_void_p]),
+    "pat_kernel_launches": (ctypes.c_ulonglong, []),
+    "pat_timing_enable": (c_int, [c_int, c_int]),
+    "pat_timing_read": (c_int, [POINTER(c_double), POINTER(ctypes.c_longlong)]),
     "pat_last_error": (c_char_p, []),
 }
 

@@ -592,6 +592,7 @@ static dim3 row_grid(const pat_plan_s* p) { return dim3((p->ng + p->R - 1) / p->
 
 int launch_medium(const Launch& L, const float* c_dom, float* cg) {
     const pat_plan_s* p = L.p;
+    count_launch();
     k_medium<<<(p->ng * p->ng + 255) / 256, 256, 0, L.st>>>(c_dom, cg, p->n, p->P, p->ng, float(p->g.c_bg));
     return check_launch("k_medium");
 }
@@ -599,40 +600,52 @@ int launch_medium(const Launch& L, const float* c_dom, float* cg) {
 int launch_row_rho(const Launch& L, const Ws& w, int mode, const float* p0, float* y, int tstep, float* hist,
                    int hist_slot) {
     const pat_plan_s* p = L.p;
+    prof_begin(PAT_K_ROW_RHO, L.st);
     k_row_rho<<<row_grid(p), 256, p->smem_row, L.st>>>(geo(p), w.A, w.B, w.rx, w.ry, w.cg, mode, p0, y, tstep,
                                                        hist, hist_slot, p->R);
+    prof_end(PAT_K_ROW_RHO, L.st);
     return check_launch("k_row_rho");
 }
 
 int launch_row_u(const Launch& L, const Ws& w, int init) {
     const pat_plan_s* p = L.p;
+    prof_begin(PAT_K_ROW_U, L.st);
     k_row_u<<<row_grid(p), 256, p->smem_row, L.st>>>(geo(p), w.A, w.B, w.ux, w.uy, init, p->R);
+    prof_end(PAT_K_ROW_U, L.st);
     return check_launch("k_row_u");
 }
 
 int launch_col(const Launch& L, float2* A, float2* B, int mode, int op, float scale) {
     const pat_plan_s* p = L.p;
     dim3 grid((p->hc + p->C - 1) / p->C, p->K);
+    const int cls = mode == 0 ? PAT_K_COL_GRAD : (mode == 1 ? PAT_K_COL_PAIR : PAT_K_COL_SUM);
+    prof_begin(cls, L.st);
     k_col<<<grid, 256, p->smem_col, L.st>>>(geo(p), A, B, mode, op, scale, p->C);
+    prof_end(cls, L.st);
     return check_launch("k_col");
 }
 
 int launch_row_adj_rho(const Launch& L, const Ws& w, int first, const float* resid, int tstep, const float* hist,
                        int hist_slot) {
     const pat_plan_s* p = L.p;
+    prof_begin(PAT_K_ROW_ADJ_RHO, L.st);
     k_row_adj_rho<<<row_grid(p), 256, p->smem_row, L.st>>>(geo(p), w.A2, w.B2, w.rbx, w.rby, w.cbar, w.cg, first,
                                                            resid, tstep, hist, hist_slot, p->R);
+    prof_end(PAT_K_ROW_ADJ_RHO, L.st);
     return check_launch("k_row_adj_rho");
 }
 
 int launch_row_adj_u(const Launch& L, const Ws& w) {
     const pat_plan_s* p = L.p;
+    prof_begin(PAT_K_ROW_ADJ_U, L.st);
     k_row_adj_u<<<row_grid(p), 256, p->smem_row, L.st>>>(geo(p), w.A2, w.B2, w.ubx, w.uby, p->R);
+    prof_end(PAT_K_ROW_ADJ_U, L.st);
     return check_launch("k_row_adj_u");
 }
 
 int launch_row_adj_final1(const Launch& L, const Ws& w, int first, const float* resid, float* grad_p0) {
     const pat_plan_s* p = L.p;
+    count_launch();
     k_row_adj_final1<<<row_grid(p), 256, p->smem_row, L.st>>>(geo(p), w.A2, w.B2, w.ubx, w.uby, first, resid,
                                                               grad_p0, p->R);
     return check_launch("k_row_adj_final1");
@@ -640,6 +653,7 @@ int launch_row_adj_final1(const Launch& L, const Ws& w, int first, const float* 
 
 int launch_row_adj_final2(const Launch& L, const Ws& w, const float* p0, float* grad_p0) {
     const pat_plan_s* p = L.p;
+    count_launch();
     k_row_adj_final2<<<row_grid(p), 256, p->smem_row, L.st>>>(geo(p), w.A2, w.rbx, w.rby, w.cg, p0, grad_p0,
                                                               w.cbar, p->R);
     return check_launch("k_row_adj_final2");
@@ -648,6 +662,7 @@ int launch_row_adj_final2(const Launch& L, const Ws& w, const float* p0, float* 
 int launch_reduce_cbar(const Launch& L, const Ws& w, float* grad_c) {
     const pat_plan_s* p = L.p;
     const int nn = p->n * p->n;
+    count_launch();
     k_reduce_cbar<<<(nn + 255) / 256, 256, 0, L.st>>>(w.cbar, grad_c, p->K, nn);
     return check_launch("k_reduce_cbar");
 }
@@ -656,9 +671,11 @@ int launch_residual(const Launch& L, const Ws& w, const float* ypred, const floa
                     float* resid, double* J_out) {
     const pat_plan_s* p = L.p;
     PAT_CUDA(cudaMemsetAsync(w.flag, 0, sizeof(int), L.st));
+    count_launch();
     k_residual<<<kPartials, 256, 0, L.st>>>(ypred, ymeas, wts, resid, p->K, p->nt * p->m, w.part, w.flag);
     int rc = check_launch("k_residual");
     if (rc) return rc;
+    count_launch();
     k_sum_partials<<<1, 32, 0, L.st>>>(w.part, kPartials, J_out ? J_out : w.J, w.flag);
     return check_launch("k_sum_partials");
 }

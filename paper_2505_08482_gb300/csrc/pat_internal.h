@@ -77,6 +77,11 @@ namespace pat {
 
 Ws resolve(const pat_plan_s* p, void* base, bool grad);
 
+// launch accounting / optional event timing of one kernel class (timing.cu)
+void count_launch();
+void prof_begin(int cls, cudaStream_t st);
+void prof_end(int cls, cudaStream_t st);
+
 // ---- kernel launchers (kernels.cu) ----
 struct Launch {
     const pat_plan_s* p;

@@ -33,7 +33,7 @@ static bool smooth235(int n) {
     return n == 1;
 }
 
-static bool grid_ok(int ng) { return ng >= 4 && ng <= 1024 && ng % 4 == 0 && smooth235(ng); }
+static bool grid_ok(int ng) { return ng >= 4 && ng <= 1024 && ng % 2 == 0 && smooth235(ng); }
 
 // Radix schedule: as many radix-4 stages as possible, then 5, 3, 2.
 static bool radix_schedule(int n, FftDesc* fd) {
@@ -153,7 +153,7 @@ extern "C" int pat_plan_create(pat_plan* out, const pat_grid* g, int m, const do
     }
     const int ng = g->n + 2 * g->pml;
     if (!grid_ok(ng)) {
-        set_error("pat_plan_create: grid side n+2*pml = %d must be a multiple of 4, 5-smooth and <= 1024", ng);
+        set_error("pat_plan_create: grid side n+2*pml = %d must be even, 5-smooth and <= 1024", ng);
         return PAT_EINVAL;
     }
     pat_plan_s* p = new pat_plan_s();

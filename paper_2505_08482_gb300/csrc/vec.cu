@@ -164,12 +164,14 @@ static unsigned blocks_for(size_t n) {
 }
 
 static int chk(const char* w) {
+    count_launch();
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? PAT_OK : cuda_fail(e, w);
 }
 
 int vdot(cudaStream_t st, const float* a, const float* b, size_t n, double* out, double* part,
          const double* scale, double mul) {
+    count_launch();
     k_dot_partial<<<kPartials, 256, 0, st>>>(a, b, n, part);
     k_dot_final<<<1, 32, 0, st>>>(part, kPartials, out, scale, mul);
     return chk("vdot");
@@ -208,6 +210,7 @@ int vclip_dir(cudaStream_t st, float* d, const float* z, size_t n, size_t n0, co
 }
 
 int vabsmax(cudaStream_t st, const float* a, size_t n, double* out, double* part) {
+    count_launch();
     k_absmax_partial<<<kPartials, 256, 0, st>>>(a, n, part);
     k_max_final<<<1, 32, 0, st>>>(part, kPartials, out);
     return chk("vabsmax");

@@ -166,3 +166,62 @@ class Plan:
         ws = self.workspace(B.PAT_WS_GRADIENT)
         B.check(B.lib().pat_status(self._h, _ptr(ws), ctypes.byref(flag), _stream(stream)), "pat_status")
         return bool(flag.value)
+
+
+@dataclass
+class ReconConfig:
+    """Parameters of pat_reconstruct (see include/pat.h)."""
+    levels: tuple
+    L: float
+    dt_data: float
+    nt_data: int
+    sensors_xy: object
+    K: int
+    cfl: float = 0.3
+    c_lo: float = 1350.0
+    c_hi: float = 1750.0
+    p0_lo: float = 0.0
+    c_bg: float = 1500.0
+    rho0: float = 1000.0
+    pml_alpha: float = 2.0
+    min_pml: int = 20
+    mem: int = 20
+    iters: int = 20
+    max_halvings: int = 20
+    ckpt_every: int = 32
+    rtol: float = 1e-4
+    alpha0: float = 0.1
+    c1: float = 1e-4
+    sigma_p0: float = 0.25
+
+
+def reconstruct(cfg: ReconConfig, y_meas, w, c_init, p0_init=None, stream=None, max_report=4096):
+    """Joint reconstruction (pat_reconstruct).  Returns (c, p0, report rows, status, total_ms).
+
+    ``c_init``/``p0_init`` are device tensors on the finest level ([N][N] and
+    [K][N][N]); they are copied, not modified.
+    """
+    N = int(cfg.levels[-1])
+    K = int(cfg.K)
+    dev = y_meas.device
+    c = c_init.detach().clone().contiguous()
+    p0 = torch.zeros((K, N, N), dtype=torch.float32, device=dev) if p0_init is None else \
+        p0_init.detach().clone().contiguous()
+    _f32(c, (N, N), "c_init", dev)
+    _f32(p0, (K, N, N), "p0_init", dev)
+    xy = np.ascontiguousarray(np.asarray(cfg.sensors_xy, dtype=np.float64))
+    _f32(y_meas, (K, cfg.nt_data, xy.shape[0]), "y_meas", dev)
+    _f32(w, (K,), "w", dev)
+    lv = (ctypes.c_int * len(cfg.levels))(*[int(v) for v in cfg.levels])
+    c_cfg = B.PatReconCfg(len(cfg.levels), lv, cfg.L, cfg.dt_data, cfg.nt_data, xy.shape[0],
+                          xy.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), K, cfg.cfl, cfg.c_lo, cfg.c_hi,
+                          cfg.p0_lo, cfg.c_bg, cfg.rho0, cfg.pml_alpha, cfg.min_pml, cfg.mem, cfg.iters,
+                          cfg.max_halvings, cfg.ckpt_every, cfg.rtol, cfg.alpha0, cfg.c1, cfg.sigma_p0)
+    rows = (B.PatIterReport * max_report)()
+    rep = B.PatReport(max_report, 0, rows, 0, 0.0)
+    with torch.cuda.device(dev):
+        B.check(B.lib().pat_reconstruct(ctypes.byref(c_cfg), _ptr(y_meas), _ptr(w), _ptr(c), _ptr(p0),
+                                        ctypes.byref(rep), _stream(stream)), "pat_reconstruct")
+    out = [dict(level=r.level, it=r.iter, J=r.J, gnorm=r.gnorm, alpha=r.alpha, trials=r.trials, J_new=r.J_new,
+                ms=r.ms) for r in rows[:rep.count]]
+    return c, p0, out, int(rep.status), float(rep.total_ms)

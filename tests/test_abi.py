@@ -40,6 +40,11 @@ def test_library_loads_and_host_helpers(libpath):
     assert L.pat_pml_auto(64, 20) == 22
     assert L.pat_pml_auto(256, 20) == 22
     assert L.pat_pml_auto(160, 20) == 20
+    assert L.pat_pml_auto(50, 20) == 20        # Ng = 90 = 2 * 3^2 * 5
+    from oracle.grid import pml_auto
+    for n in range(2, 300, 2):
+        assert L.pat_pml_auto(n, 20) == pml_auto(n, 20)
+    assert L.pat_pml_auto(63, 20) == -1
     assert L.pat_plan_ng(None) == -1
     assert L.pat_workspace_bytes(None, 0) == 0
 
@@ -49,10 +54,13 @@ def test_plan_create_rejects_bad_grids_before_touching_the_device(libpath):
     L = B.lib()
     xy = (ctypes.c_double * 2)(0.0032, 0.0032)
     h = ctypes.c_void_p()
-    # 64 + 2*21 = 106 is not a multiple of 4
+    # 64 + 2*21 = 106 = 2 * 53 is not 5-smooth
     g = B.PatGrid(64, 21, 1e-4, 1e-8, 10, 1750.0, 1000.0, 2.0, 1500.0)
     assert L.pat_plan_create(ctypes.byref(h), ctypes.byref(g), 1, xy, 1, 32) == B.PAT_EINVAL
-    assert b"multiple of 4" in L.pat_last_error()
+    assert b"5-smooth" in L.pat_last_error()
+    # odd grid side: 63 + 2*21 = 105
+    g = B.PatGrid(63, 21, 1e-4, 1e-8, 10, 1750.0, 1000.0, 2.0, 1500.0)
+    assert L.pat_plan_create(ctypes.byref(h), ctypes.byref(g), 1, xy, 1, 32) == B.PAT_EINVAL
     # 7-smooth but not 5-smooth: 64 + 2*6 = 76 = 4 * 19
     g = B.PatGrid(64, 6, 1e-4, 1e-8, 10, 1750.0, 1000.0, 2.0, 1500.0)
     assert L.pat_plan_create(ctypes.byref(h), ctypes.byref(g), 1, xy, 1, 32) == B.PAT_EINVAL

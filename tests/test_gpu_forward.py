@@ -46,9 +46,9 @@ def test_forward_ragged_multi_k_matches_oracle():
         assert rel_l2(y[k], ref[k]) <= 1e-4
 
 
-@pytest.mark.parametrize("n,pml", [(16, 8), (12, 12), (20, 20), (100, 22), (8, 10)])
+@pytest.mark.parametrize("n,pml", [(16, 8), (12, 12), (20, 20), (100, 22), (50, 20), (8, 10)])
 def test_forward_other_grid_sizes(n, pml):
-    # Ng = 32 (radix 4,4,2), 36, 60, 144; Ng = 28 has the factor 7 and is rejected
+    # Ng = 32 (radix 4,4,2), 36, 60, 144, 90 (= 2 mod 4); Ng = 28 has the factor 7 and is rejected
     from paper_2505_08482_gb300 import _binding as B
     from oracle.grid import is_smooth
     ng = n + 2 * pml
