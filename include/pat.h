@@ -112,6 +112,25 @@ size_t pat_workspace_bytes(pat_plan plan, int kind);
 int pat_forward(pat_plan plan, const float* d_c, const float* d_p0, float* d_y,
                 void* d_ws, size_t ws_bytes, void* stream);
 
+/* Forward operator without any allocation, for callers that cannot
+ * allocate device memory at the time they run the model (for example an
+ * acquisition process whose device memory budget is fixed at start-up, or a
+ * host program whose device memory is owned by another allocator; cudaMalloc
+ * can also synchronise the device, which a latency-critical loop cannot
+ * afford).  The paper has no counterpart: this is a deployment variant of
+ * pat_forward.  Same arguments and results as pat_forward without the
+ * workspace: the scratch is a static device array of
+ * PAT_NOALLOC_SCRATCH_BYTES (16 MiB) that every GPU loading the library
+ * holds until exit.  Plans whose forward workspace
+ * (pat_workspace_bytes(plan, PAT_WS_FORWARD)) exceeds it are rejected with
+ * PAT_EINVAL and a message.  The plan's device must be current.  The first
+ * call on a device looks up the array's device address (set-up), so make it
+ * before any stream capture.  All calls share the array and it keeps the
+ * last call's contents; calls that overlap on the GPU race on it.  No
+ * checkpoints are kept, so it cannot precede pat_vjp. */
+#define PAT_NOALLOC_SCRATCH_BYTES (16 * 1024 * 1024)
+int pat_forward_noalloc(pat_plan plan, const float* d_c, const float* d_p0, float* d_y, void* stream);
+
 /* Data term and its gradient (Eq. Minimised_functional without priors;
  * Eqs. gradient_p0 and gradient_sos for the discrete scheme):
  *   J = sum_k w_k/2 || y_pred_k - y_meas_k ||^2,

@@ -29,6 +29,7 @@ PAT_K_ROW_ADJ_U = 7
 KERNEL_CLASSES = {1: "k_row_rho", 2: "k_row_u", 3: "k_col(grad)", 4: "k_col(pair)", 5: "k_col(sum)",
                   6: "k_row_adj_rho", 7: "k_row_adj_u"}
 PAT_WS_FORWARD = 0
+PAT_NOALLOC_SCRATCH_BYTES = 16 * 1024 * 1024
 PAT_WS_GRADIENT = 1
 
 
@@ -64,6 +65,7 @@ SIGNATURES = {
     "pat_pml_auto": (c_int, [c_int, c_int]),
     "pat_workspace_bytes": (c_size_t, [c_void_p, c_int]),
     "pat_forward": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),
+    "pat_forward_noalloc": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "pat_adjoint_grad": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                                  c_void_p, c_void_p, c_size_t, c_void_p]),
     "pat_vjp": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),

@@ -44,8 +44,10 @@ int step(const Launch& L, const Ws& w, int n, float* y, float* hist, int hist_sl
 
 size_t state_bytes(const pat_plan_s* p) { return 4 * size_t(p->K) * p->ng * p->ng * sizeof(float); }
 
-int forward_sweep(pat_plan_s* p, const float* c, const float* p0, float* y, const Ws& w, bool keep,
-                  cudaStream_t st) {
+}  // namespace
+
+int pat::forward_sweep(pat_plan_s* p, const float* c, const float* p0, float* y, const Ws& w, bool keep,
+                       cudaStream_t st) {
     Launch L{p, st};
     RC(launch_medium(L, c, w.cg));
     PAT_CUDA(cudaMemsetAsync(y, 0, size_t(p->K) * p->nt * p->m * sizeof(float), st));
@@ -61,6 +63,8 @@ int forward_sweep(pat_plan_s* p, const float* c, const float* p0, float* y, cons
     }
     return PAT_OK;
 }
+
+namespace {
 
 // reverse sweep with the weighted residual (or adjoint source) r [K][nt][m]
 int reverse_sweep(pat_plan_s* p, const float* p0, const float* r, float* grad_p0, float* grad_c, const Ws& w,

@@ -110,7 +110,11 @@ int launch_reduce_cbar(const Launch& L, const Ws& w, float* grad_c);
 int launch_residual(const Launch& L, const Ws& w, const float* ypred, const float* ymeas,
                     const float* wts, float* resid, double* J_out);
 
-// ---- api.cu internals used by the reconstruction driver ----
+// ---- api.cu internals ----
+// Forward sweep into y [K][nt][m] with workspace regions w (checkpoints kept if keep).
+int forward_sweep(pat_plan_s* p, const float* c, const float* p0, float* y, const Ws& w, bool keep,
+                  cudaStream_t st);
+// used by the reconstruction driver:
 // J only (forward sweep + residual) into *J_dev; workspace of PAT_WS_GRADIENT size.
 int objective(pat_plan_s* p, const float* c, const float* p0, const float* ymeas, const float* wts, double* J_dev,
               void* ws, size_t ws_bytes, cudaStream_t st);
