@@ -92,6 +92,18 @@ void pat_plan_destroy(pat_plan plan);
 /* FFT grid side Ng and PML width of a plan (for callers that size buffers). */
 int pat_plan_ng(pat_plan plan);
 
+/* Kernel variants of a plan.  Grid sides with a compiled two-level FFT
+ * (108, 144, 180, 200, 240, 300) have fixed-size passes in several tile
+ * shapes (variant 0: 4 rows / 4 spectral columns per CTA, variant 1: 8 rows /
+ * 2 columns); every side also has the generic shared-memory Stockham passes
+ * (variant -1).  All variants compute the same scheme.  A new plan uses
+ * variant 0 when it exists, else -1.  pat_plan_variants returns the number of
+ * fixed-size variants; pat_plan_set_variant selects one (PAT_EINVAL if it
+ * does not exist); pat_plan_variant returns the current one. */
+int pat_plan_variants(pat_plan plan);
+int pat_plan_set_variant(pat_plan plan, int variant);
+int pat_plan_variant(pat_plan plan);
+
 /* Smallest PML width >= min_pml for which n + 2 P satisfies the grid rules
  * above (Sec. 4.1.1: PML sized so the grid has small prime factors);
  * returns -1 if none <= 1024 exists. */
@@ -242,10 +254,12 @@ int pat_reconstruct(const pat_recon_cfg* cfg, const float* d_y_meas, const float
 /* Total number of kernels this library has launched in the process. */
 unsigned long long pat_kernel_launches(void);
 
-/* Record a pair of CUDA events on the launching stream around each of the
- * next max_launches launches of kernel class cls (0 disables).  Events are
- * created here, outside any timed region. */
-int pat_timing_enable(int cls, int max_launches);
+/* Record a pair of CUDA events on the launching stream around every
+ * every-th launch of kernel class cls (at most max_launches pairs; cls 0
+ * disables).  Events are created here, outside any timed region.  Sampling
+ * keeps the perturbation of the timed work small: an event between two
+ * kernels removes their programmatic launch overlap. */
+int pat_timing_enable(int cls, int max_launches, int every);
 
 /* Sum of the recorded launch durations (ms) and their count; waits for the
  * last recorded event and resets the counter. */

@@ -62,6 +62,9 @@ SIGNATURES = {
     "pat_plan_create": (c_int, [POINTER(c_void_p), POINTER(PatGrid), c_int, POINTER(c_double), c_int, c_int]),
     "pat_plan_destroy": (None, [c_void_p]),
     "pat_plan_ng": (c_int, [c_void_p]),
+    "pat_plan_variants": (c_int, [c_void_p]),
+    "pat_plan_set_variant": (c_int, [c_void_p, c_int]),
+    "pat_plan_variant": (c_int, [c_void_p]),
     "pat_pml_auto": (c_int, [c_int, c_int]),
     "pat_workspace_bytes": (c_size_t, [c_void_p, c_int]),
     "pat_forward": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),
@@ -73,7 +76,7 @@ SIGNATURES = {
     "pat_reconstruct": (c_int, [POINTER(PatReconCfg), c_void_p, c_void_p, c_void_p, c_void_p, POINTER(PatReport),
                                 c_void_p]),
     "pat_kernel_launches": (ctypes.c_ulonglong, []),
-    "pat_timing_enable": (c_int, [c_int, c_int]),
+    "pat_timing_enable": (c_int, [c_int, c_int, c_int]),
     "pat_timing_read": (c_int, [POINTER(c_double), POINTER(ctypes.c_longlong)]),
     "pat_last_error": (c_char_p, []),
 }

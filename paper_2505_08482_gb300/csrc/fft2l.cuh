@@ -1,0 +1,171 @@
+// Two-level register FFT for a compile-time length N = N1 * N2 (both small,
+// 5-smooth).  A length-N transform is split as in the Cooley-Tukey
+// factorisation
+//   X[k1 + N1 k2] = sum_{n2} W_{N2}^{n2 k2} W_N^{n2 k1} sum_{n1} x[N2 n1 + n2] W_{N1}^{n1 k1}
+// so that one thread ("A layout", index n2) holds x[N2 n1 + n2] for all n1
+// and does a register DFT of length N1, and after one shared-memory
+// transpose another thread ("B layout", index k1) holds the values for all n2
+// and does a register DFT of length N2, ending with X[k1 + N1 k2].  The
+// inverse runs the same two steps backwards (B layout -> A layout), so a
+// forward transform, a pointwise product in wavenumber space and an inverse
+// transform need only two shared-memory transposes.
+//
+// Register DFTs of composite lengths are built recursively from radix 2/3/4/5
+// with twiddles evaluated at compile time (constexpr Taylor series).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <type_traits>
+
+#include "fft.cuh"
+
+namespace pat {
+
+// ---- compile-time trigonometry (Taylor series after reduction to [-pi, pi]) ----
+__host__ __device__ constexpr double ce_reduce(double a) {
+    constexpr double PI = 3.14159265358979323846264338327950288;
+    while (a > PI) a -= 2.0 * PI;
+    while (a < -PI) a += 2.0 * PI;
+    return a;
+}
+__host__ __device__ constexpr double ce_sin(double a) {
+    a = ce_reduce(a);
+    double term = a, sum = a;
+    for (int k = 1; k < 30; ++k) {
+        term *= -a * a / double((2 * k) * (2 * k + 1));
+        sum += term;
+    }
+    return sum;
+}
+__host__ __device__ constexpr double ce_cos(double a) {
+    a = ce_reduce(a);
+    double term = 1.0, sum = 1.0;
+    for (int k = 1; k < 30; ++k) {
+        term *= -a * a / double((2 * k - 1) * (2 * k));
+        sum += term;
+    }
+    return sum;
+}
+
+template <int B, int E, class F>
+__host__ __device__ __forceinline__ void static_for(F&& f) {
+    if constexpr (B < E) {
+        f(std::integral_constant<int, B>{});
+        static_for<B + 1, E>(f);
+    }
+}
+
+// z * W_N^E, W_N = exp(-2 pi i / N) (forward) or exp(+2 pi i / N) (inverse); E compile-time
+template <int N, int E, bool INV>
+__host__ __device__ __forceinline__ float2 twc(float2 z) {
+    constexpr int e = E % N;
+    if constexpr (e == 0) {
+        return z;
+    } else if constexpr (2 * e == N) {
+        return make_float2(-z.x, -z.y);
+    } else if constexpr (4 * e == N) {
+        return rot<INV>(z);
+    } else if constexpr (4 * e == 3 * N) {
+        return rot<!INV>(z);
+    } else {
+        constexpr double PI = 3.14159265358979323846264338327950288;
+        constexpr double a = (INV ? 2.0 : -2.0) * PI * double(e) / double(N);
+        constexpr float c = float(ce_cos(a));
+        constexpr float s = float(ce_sin(a));
+        return make_float2(z.x * c - z.y * s, z.x * s + z.y * c);
+    }
+}
+
+template <int N, bool INV>
+__host__ __device__ __forceinline__ void dft(float2 (&v)[N]);
+
+// N = A * B: DFT_A over a of v[B a + b] for each b, twiddle W_N^{b ka}, DFT_B over b
+template <int A, int B, bool INV>
+__host__ __device__ __forceinline__ void dft_ab(float2 (&v)[A * B]) {
+    constexpr int N = A * B;
+    float2 t[N];
+    static_for<0, B>([&](auto bI) {
+        constexpr int b = decltype(bI)::value;
+        float2 u[A];
+        static_for<0, A>([&](auto aI) { u[decltype(aI)::value] = v[B * decltype(aI)::value + b]; });
+        dft<A, INV>(u);
+        static_for<0, A>([&](auto kI) {
+            constexpr int ka = decltype(kI)::value;
+            t[ka * B + b] = twc<N, b * ka, INV>(u[ka]);
+        });
+    });
+    static_for<0, A>([&](auto kI) {
+        constexpr int ka = decltype(kI)::value;
+        float2 u[B];
+        static_for<0, B>([&](auto bI) { u[decltype(bI)::value] = t[ka * B + decltype(bI)::value]; });
+        dft<B, INV>(u);
+        static_for<0, B>([&](auto kbI) { v[ka + A * decltype(kbI)::value] = u[decltype(kbI)::value]; });
+    });
+}
+
+template <int N, bool INV>
+__host__ __device__ __forceinline__ void dft(float2 (&v)[N]) {
+    if constexpr (N == 1) {
+    } else if constexpr (N == 2 || N == 3 || N == 4 || N == 5) {
+        dft_small<N, INV>(v);
+    } else if constexpr (N % 4 == 0) {
+        dft_ab<4, N / 4, INV>(v);
+    } else if constexpr (N % 2 == 0) {
+        dft_ab<2, N / 2, INV>(v);
+    } else if constexpr (N % 3 == 0) {
+        dft_ab<3, N / 3, INV>(v);
+    } else {
+        static_assert(N % 5 == 0, "length must be 5-smooth");
+        dft_ab<5, N / 5, INV>(v);
+    }
+}
+
+// Shapes of the two-level transform of length N = N1 * N2.
+template <int N1_, int N2_>
+struct Fft2 {
+    static constexpr int N1 = N1_;
+    static constexpr int N2 = N2_;
+    static constexpr int N = N1 * N2;
+    static constexpr int T = N1 > N2 ? N1 : N2;   // threads per sequence
+    static constexpr int P2 = (N2 % 2) ? N2 : N2 + 1;   // padded row of the transpose buffer
+    static constexpr int ZS = N1 * P2;            // transpose buffer elements per sequence
+
+    // Z element (k1, n2) lives at Z[(k1 P2 + n2) S] (S interleaves several transforms).
+    // forward, A layout: a[n1] = x[N2 n1 + n2] -> a[k1] twiddled, stored to Z(k1, n2)
+    template <int S = 1>
+    __host__ __device__ static __forceinline__ void fwd_a(float2 (&a)[N1], int n2, float2* Z, const float2* tw) {
+        dft<N1, false>(a);
+        static_for<0, N1>([&](auto kI) {
+            constexpr int k1 = decltype(kI)::value;
+            float2 v = a[k1];
+            if constexpr (k1 > 0) v = cmul(v, tw[n2 * k1]);
+            Z[(k1 * P2 + n2) * S] = v;
+        });
+    }
+    // forward, B layout: b[n2] = Z[k1 P2 + n2] -> b[k2] = X[k1 + N1 k2]
+    template <int S = 1>
+    __host__ __device__ static __forceinline__ void fwd_b_load(float2 (&b)[N2], int k1, const float2* Z) {
+        static_for<0, N2>([&](auto nI) { b[decltype(nI)::value] = Z[(k1 * P2 + decltype(nI)::value) * S]; });
+    }
+    __host__ __device__ static __forceinline__ void fwd_b(float2 (&b)[N2]) { dft<N2, false>(b); }
+    // inverse, B layout: b[k2] = X[k1 + N1 k2] -> inverse DFT_N2, twiddle, Z[k1 P2 + n2]
+    template <int S = 1>
+    __host__ __device__ static __forceinline__ void inv_b(float2 (&b)[N2], int k1, float2* Z, const float2* tw) {
+        dft<N2, true>(b);
+        static_for<0, N2>([&](auto nI) {
+            constexpr int n2 = decltype(nI)::value;
+            float2 v = b[n2];
+            if constexpr (n2 > 0) v = cmulc(v, tw[n2 * k1]);
+            Z[(k1 * P2 + n2) * S] = v;
+        });
+    }
+    // inverse, A layout: a[k1] = Z[k1 P2 + n2] -> inverse DFT_N1 -> a[n1] = x[n2 + N2 n1]
+    template <int S = 1>
+    __host__ __device__ static __forceinline__ void inv_a_load(float2 (&a)[N1], int n2, const float2* Z) {
+        static_for<0, N1>([&](auto kI) { a[decltype(kI)::value] = Z[(decltype(kI)::value * P2 + n2) * S]; });
+    }
+    __host__ __device__ static __forceinline__ void inv_a(float2 (&a)[N1]) { dft<N1, true>(a); }
+};
+
+}  // namespace pat

@@ -1,0 +1,27 @@
+// Registry of the fixed-size passes: grid sides with a compiled two-level FFT.
+#include "kfixed.cuh"
+
+namespace pat {
+
+const FixedOps* fixed_ops_108(int v);
+const FixedOps* fixed_ops_144(int v);
+const FixedOps* fixed_ops_180(int v);
+const FixedOps* fixed_ops_200(int v);
+const FixedOps* fixed_ops_240(int v);
+const FixedOps* fixed_ops_300(int v);
+
+const FixedOps* fixed_ops_for(int ng, int v) {
+    switch (ng) {
+        case 108: return fixed_ops_108(v);
+        case 144: return fixed_ops_144(v);
+        case 180: return fixed_ops_180(v);
+        case 200: return fixed_ops_200(v);
+        case 240: return fixed_ops_240(v);
+        case 300: return fixed_ops_300(v);
+        default: return nullptr;
+    }
+}
+
+int fixed_variants(int ng) { return fixed_ops_for(ng, 0) ? 2 : 0; }
+
+}  // namespace pat

@@ -17,57 +17,10 @@
 #include <cstdint>
 
 #include "pat_internal.h"
+#include "geo.cuh"
+#include "kfixed.cuh"
 
 namespace pat {
-
-// Per-plan constants passed by value.
-struct Geo {
-    int ng, hc, n, P, K, nt, m, s_eff;
-    FftDesc fft;
-    const float2* tw;
-    const float* kappa_t;
-    const float2* fx;
-    const float2* fy;
-    const float* a_cell;
-    const float* a_stag;
-    const int* srow;
-    const int2* sent;
-    const float4* sentw;
-};
-
-static Geo geo(const pat_plan_s* p) {
-    Geo g;
-    g.ng = p->ng; g.hc = p->hc; g.n = p->n; g.P = p->P; g.K = p->K; g.nt = p->nt; g.m = p->m;
-    g.s_eff = p->s_eff;
-    g.fft = p->fft;
-    g.tw = p->t.tw; g.kappa_t = p->t.kappa_t; g.fx = p->t.fx; g.fy = p->t.fy;
-    g.a_cell = p->t.a_cell; g.a_stag = p->t.a_stag;
-    g.srow = p->t.srow; g.sent = p->t.sent; g.sentw = p->t.sentw;
-    return g;
-}
-
-__device__ __forceinline__ void load_twiddles(float2* tw, const Geo& g) {
-    for (int i = threadIdx.x; i < g.ng; i += blockDim.x) tw[i] = g.tw[i];
-}
-
-// z[j][.] = full spectrum of a_j + i b_j from the half spectra a_j, b_j
-// (bins 0 and Ng/2 keep their real parts only: the rows are real).
-__device__ __forceinline__ void put_c2r(float2* zrow, int ng, int kx, float2 a, float2 b) {
-    if (kx == 0 || 2 * kx == ng) {
-        a.y = 0.f;
-        b.y = 0.f;
-    }
-    zrow[kx] = make_float2(a.x - b.y, a.y + b.x);
-    if (kx > 0 && 2 * kx < ng) zrow[ng - kx] = make_float2(a.x + b.y, b.x - a.y);
-}
-
-// Split the FFT of a + i b into the half spectra of a and b at bin kx.
-__device__ __forceinline__ void get_r2c(const float2* zrow, int ng, int kx, float2& A, float2& B) {
-    const float2 zk = zrow[kx];
-    const float2 zm = zrow[kx == 0 ? 0 : ng - kx];
-    A = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
-    B = make_float2(0.5f * (zk.y + zm.y), -0.5f * (zk.x - zm.x));
-}
 
 // ---------------------------------------------------------------------------
 // forward: row pass producing rho^{n+1}, p^{n+1}
@@ -95,7 +48,7 @@ __global__ void __launch_bounds__(256) k_row_rho(Geo g, float2* __restrict__ A, 
     if (mode == 0) {
         for (int i = threadIdx.x; i < nr * hc; i += blockDim.x) {
             const int r = i / hc, kx = i - r * hc;
-            const size_t gi = (size_t(k) * ng + y0 + r) * hc + kx;
+            const size_t gi = (size_t(k) * ng + y0 + r) * g.hp + kx;
             put_c2r(z + r * ng, ng, kx, A[gi], B[gi]);
         }
         __syncthreads();
@@ -162,8 +115,8 @@ __global__ void __launch_bounds__(256) k_row_rho(Geo g, float2* __restrict__ A, 
         const int j = i / hc, kx = i - j * hc;
         float2 a, b;
         get_r2c(res2 + j * ng, ng, kx, a, b);
-        A[(size_t(k) * ng + y0 + 2 * j) * hc + kx] = a;
-        A[(size_t(k) * ng + y0 + 2 * j + 1) * hc + kx] = b;
+        A[(size_t(k) * ng + y0 + 2 * j) * g.hp + kx] = a;
+        A[(size_t(k) * ng + y0 + 2 * j + 1) * g.hp + kx] = b;
     }
 }
 
@@ -182,7 +135,7 @@ __global__ void __launch_bounds__(256) k_row_u(Geo g, float2* __restrict__ A, fl
     load_twiddles(tw, g);
     for (int i = threadIdx.x; i < nr * hc; i += blockDim.x) {
         const int r = i / hc, kx = i - r * hc;
-        const size_t gi = (size_t(k) * ng + y0 + r) * hc + kx;
+        const size_t gi = (size_t(k) * ng + y0 + r) * g.hp + kx;
         put_c2r(z + r * ng, ng, kx, A[gi], B[gi]);
     }
     __syncthreads();
@@ -208,7 +161,7 @@ __global__ void __launch_bounds__(256) k_row_u(Geo g, float2* __restrict__ A, fl
         const int r = i / hc, kx = i - r * hc;
         float2 a, b;
         get_r2c(res2 + r * ng, ng, kx, a, b);
-        const size_t gi = (size_t(k) * ng + y0 + r) * hc + kx;
+        const size_t gi = (size_t(k) * ng + y0 + r) * g.hp + kx;
         A[gi] = a;
         B[gi] = b;
     }
@@ -236,7 +189,7 @@ __global__ void __launch_bounds__(256) k_col(Geo g, float2* __restrict__ A, floa
         const int src = rest / ng;
         const int kx = kx0 + c;
         float2 v = make_float2(0.f, 0.f);
-        if (kx < hc) v = (src == 0 ? A : B)[(size_t(k) * ng + ky) * hc + kx];
+        if (kx < hc) v = (src == 0 ? A : B)[(size_t(k) * ng + ky) * g.hp + kx];
         b0[(src * C + c) * ng + ky] = v;
     }
     __syncthreads();
@@ -276,7 +229,7 @@ __global__ void __launch_bounds__(256) k_col(Geo g, float2* __restrict__ A, floa
         const int ky = rest % ng;
         const int dst = rest / ng;
         const int kx = kx0 + c;
-        if (kx < hc) (dst == 0 ? A : B)[(size_t(k) * ng + ky) * hc + kx] = res2[(dst * C + c) * ng + ky];
+        if (kx < hc) (dst == 0 ? A : B)[(size_t(k) * ng + ky) * g.hp + kx] = res2[(dst * C + c) * ng + ky];
     }
 }
 
@@ -289,8 +242,8 @@ __device__ __forceinline__ float2* c2r_rows(const Geo& g, const float2* __restri
     const int np = nr / 2;
     for (int i = threadIdx.x; i < np * hc; i += blockDim.x) {
         const int j = i / hc, kx = i - j * hc;
-        const float2 a = Q[(size_t(k) * ng + y0 + 2 * j) * hc + kx];
-        const float2 b = Q[(size_t(k) * ng + y0 + 2 * j + 1) * hc + kx];
+        const float2 a = Q[(size_t(k) * ng + y0 + 2 * j) * g.hp + kx];
+        const float2 b = Q[(size_t(k) * ng + y0 + 2 * j + 1) * g.hp + kx];
         put_c2r(z + j * ng, ng, kx, a, b);
     }
     __syncthreads();
@@ -379,7 +332,7 @@ __global__ void __launch_bounds__(256) k_row_adj_rho(Geo g, float2* __restrict__
         const int r = i / hc, kx = i - r * hc;
         float2 a, b;
         get_r2c(res2 + r * ng, ng, kx, a, b);
-        const size_t gi = (size_t(k) * ng + y0 + r) * hc + kx;
+        const size_t gi = (size_t(k) * ng + y0 + r) * g.hp + kx;
         A2[gi] = a;
         B2[gi] = b;
     }
@@ -400,7 +353,7 @@ __global__ void __launch_bounds__(256) k_row_adj_u(Geo g, float2* __restrict__ A
     load_twiddles(tw, g);
     for (int i = threadIdx.x; i < nr * hc; i += blockDim.x) {
         const int r = i / hc, kx = i - r * hc;
-        const size_t gi = (size_t(k) * ng + y0 + r) * hc + kx;
+        const size_t gi = (size_t(k) * ng + y0 + r) * g.hp + kx;
         put_c2r(z + r * ng, ng, kx, A2[gi], B2[gi]);
     }
     __syncthreads();
@@ -424,7 +377,7 @@ __global__ void __launch_bounds__(256) k_row_adj_u(Geo g, float2* __restrict__ A
         const int r = i / hc, kx = i - r * hc;
         float2 a, b;
         get_r2c(res2 + r * ng, ng, kx, a, b);
-        const size_t gi = (size_t(k) * ng + y0 + r) * hc + kx;
+        const size_t gi = (size_t(k) * ng + y0 + r) * g.hp + kx;
         A2[gi] = a;
         B2[gi] = b;
     }
@@ -470,7 +423,7 @@ __global__ void __launch_bounds__(256) k_row_adj_final1(Geo g, float2* __restric
         const int r = i / hc, kx = i - r * hc;
         float2 a, b;
         get_r2c(res2 + r * ng, ng, kx, a, b);
-        const size_t gi = (size_t(k) * ng + y0 + r) * hc + kx;
+        const size_t gi = (size_t(k) * ng + y0 + r) * g.hp + kx;
         A2[gi] = a;
         B2[gi] = b;
     }
@@ -585,6 +538,24 @@ int configure_kernels(pat_plan_s* p) {
         PAT_CUDA(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, int(p->smem_row)));
     PAT_CUDA(cudaFuncSetAttribute((const void*)k_col, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   int(p->smem_col)));
+    return select_variant(p, fixed_variants(p->ng) > 0 ? 0 : -1);
+}
+
+int select_variant(pat_plan_s* p, int variant) {
+    if (variant < 0) {
+        p->fast = nullptr;
+        p->variant = -1;
+        return PAT_OK;
+    }
+    const FixedOps* f = fixed_ops_for(p->ng, variant);
+    if (!f) {
+        set_error("no fixed-size variant %d for grid side %d", variant, p->ng);
+        return PAT_EINVAL;
+    }
+    int rc = f->configure();
+    if (rc != PAT_OK) return rc;
+    p->fast = f;
+    p->variant = variant;
     return PAT_OK;
 }
 
@@ -601,8 +572,11 @@ int launch_row_rho(const Launch& L, const Ws& w, int mode, const float* p0, floa
                    int hist_slot) {
     const pat_plan_s* p = L.p;
     prof_begin(PAT_K_ROW_RHO, L.st);
-    k_row_rho<<<row_grid(p), 256, p->smem_row, L.st>>>(geo(p), w.A, w.B, w.rx, w.ry, w.cg, mode, p0, y, tstep,
-                                                       hist, hist_slot, p->R);
+    if (p->fast)
+        p->fast->row_rho(geo(p), L.st, w.A, w.B, w.rx, w.ry, w.cg, mode, p0, y, tstep, hist, hist_slot);
+    else
+        k_row_rho<<<row_grid(p), 256, p->smem_row, L.st>>>(geo(p), w.A, w.B, w.rx, w.ry, w.cg, mode, p0, y,
+                                                           tstep, hist, hist_slot, p->R);
     prof_end(PAT_K_ROW_RHO, L.st);
     return check_launch("k_row_rho");
 }
@@ -610,7 +584,10 @@ int launch_row_rho(const Launch& L, const Ws& w, int mode, const float* p0, floa
 int launch_row_u(const Launch& L, const Ws& w, int init) {
     const pat_plan_s* p = L.p;
     prof_begin(PAT_K_ROW_U, L.st);
-    k_row_u<<<row_grid(p), 256, p->smem_row, L.st>>>(geo(p), w.A, w.B, w.ux, w.uy, init, p->R);
+    if (p->fast)
+        p->fast->row_u(geo(p), L.st, w.A, w.B, w.ux, w.uy, 0, init);
+    else
+        k_row_u<<<row_grid(p), 256, p->smem_row, L.st>>>(geo(p), w.A, w.B, w.ux, w.uy, init, p->R);
     prof_end(PAT_K_ROW_U, L.st);
     return check_launch("k_row_u");
 }
@@ -620,7 +597,10 @@ int launch_col(const Launch& L, float2* A, float2* B, int mode, int op, float sc
     dim3 grid((p->hc + p->C - 1) / p->C, p->K);
     const int cls = mode == 0 ? PAT_K_COL_GRAD : (mode == 1 ? PAT_K_COL_PAIR : PAT_K_COL_SUM);
     prof_begin(cls, L.st);
-    k_col<<<grid, 256, p->smem_col, L.st>>>(geo(p), A, B, mode, op, scale, p->C);
+    if (p->fast)
+        p->fast->col(geo(p), L.st, A, B, mode, op, scale);
+    else
+        k_col<<<grid, 256, p->smem_col, L.st>>>(geo(p), A, B, mode, op, scale, p->C);
     prof_end(cls, L.st);
     return check_launch("k_col");
 }
@@ -629,8 +609,12 @@ int launch_row_adj_rho(const Launch& L, const Ws& w, int first, const float* res
                        int hist_slot) {
     const pat_plan_s* p = L.p;
     prof_begin(PAT_K_ROW_ADJ_RHO, L.st);
-    k_row_adj_rho<<<row_grid(p), 256, p->smem_row, L.st>>>(geo(p), w.A2, w.B2, w.rbx, w.rby, w.cbar, w.cg, first,
-                                                           resid, tstep, hist, hist_slot, p->R);
+    if (p->fast)
+        p->fast->row_adj_rho(geo(p), L.st, w.A2, w.B2, w.rbx, w.rby, w.cbar, w.cg, first, resid, tstep, hist,
+                             hist_slot);
+    else
+        k_row_adj_rho<<<row_grid(p), 256, p->smem_row, L.st>>>(geo(p), w.A2, w.B2, w.rbx, w.rby, w.cbar, w.cg,
+                                                               first, resid, tstep, hist, hist_slot, p->R);
     prof_end(PAT_K_ROW_ADJ_RHO, L.st);
     return check_launch("k_row_adj_rho");
 }
@@ -638,7 +622,10 @@ int launch_row_adj_rho(const Launch& L, const Ws& w, int first, const float* res
 int launch_row_adj_u(const Launch& L, const Ws& w) {
     const pat_plan_s* p = L.p;
     prof_begin(PAT_K_ROW_ADJ_U, L.st);
-    k_row_adj_u<<<row_grid(p), 256, p->smem_row, L.st>>>(geo(p), w.A2, w.B2, w.ubx, w.uby, p->R);
+    if (p->fast)
+        p->fast->row_u(geo(p), L.st, w.A2, w.B2, w.ubx, w.uby, 1, 0);
+    else
+        k_row_adj_u<<<row_grid(p), 256, p->smem_row, L.st>>>(geo(p), w.A2, w.B2, w.ubx, w.uby, p->R);
     prof_end(PAT_K_ROW_ADJ_U, L.st);
     return check_launch("k_row_adj_u");
 }

@@ -1,0 +1,587 @@
+// Fixed-size passes of the k-space scheme for grid sides Ng = N1 * N2 known at
+// compile time, built on the two-level register FFT of fft2l.cuh.
+//
+// Column pass (one launch = FFT_y, k-space multiply, IFFT_y of CC spectral
+// columns per CTA): global -> registers (A layout) -> DFT_N1 -> transpose ->
+// DFT_N2 -> multiply by i k kappa e^{+-i k dx/2} -> inverse DFT_N2 ->
+// transpose -> inverse DFT_N1 -> global: two shared-memory transposes in all.
+//
+// Row passes (RR grid rows per CTA): the packed half spectra are read straight
+// into the B layout, inverse-transformed through one transpose into the A
+// layout, where each thread holds the real-space values of its row at
+// x = n2 + N2 n1 and applies the pointwise update (PML, equation of state,
+// adjoint terms); the forward transform of the updated fields goes back
+// through one transpose and a last shared-memory pass splits the two packed
+// half spectra.  Results are the same as the generic Stockham passes.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "fft2l.cuh"
+#include "geo.cuh"
+
+namespace pat {
+
+// ---------------------------------------------------------------------------
+// launch table of one fixed size / tile variant
+struct FixedOps {
+    int ng, rr, cc;
+    int (*configure)();
+    void (*col)(const Geo&, cudaStream_t, float2*, float2*, int mode, int op, float scale);
+    void (*row_u)(const Geo&, cudaStream_t, float2*, float2*, float*, float*, int kind, int init);
+    void (*row_rho)(const Geo&, cudaStream_t, float2*, const float2*, float*, float*, const float*, int mode,
+                    const float* p0, float* y, int tstep, float* hist, int hist_slot);
+    void (*row_adj_rho)(const Geo&, cudaStream_t, float2*, float2*, float*, float*, float*, const float*,
+                        int first, const float* resid, int tstep, const float* hist, int hist_slot);
+};
+
+const FixedOps* fixed_ops_for(int ng, int variant);   // nullptr if no fixed size matches
+int fixed_variants(int ng);                           // number of tile variants for ng (0 if none)
+
+// ---------------------------------------------------------------------------
+template <class F>
+__device__ __forceinline__ void load_twiddles_n(float2* tw, const Geo& g) {
+    for (int i = threadIdx.x; i < F::N; i += blockDim.x) tw[i] = g.tw[i];
+}
+
+// B layout of the packed inverse: b[k2] = Z[k1 + N1 k2] where Z is the full
+// spectrum of a + i b built from the half spectra rows ra (of a) and rb (of b).
+template <class F>
+__device__ __forceinline__ void load_c2r_b(float2 (&b)[F::N2], int k1, const float2* __restrict__ ra,
+                                           const float2* __restrict__ rb) {
+    static_for<0, F::N2>([&](auto I) {
+        constexpr int k2 = decltype(I)::value;
+        const int kx = k1 + F::N1 * k2;
+        float2 z;
+        if (2 * kx <= F::N) {
+            float2 a = ra[kx], bb = rb[kx];
+            if (kx == 0 || 2 * kx == F::N) {
+                a.y = 0.f;
+                bb.y = 0.f;
+            }
+            z = make_float2(a.x - bb.y, a.y + bb.x);
+        } else {
+            const int kk = F::N - kx;
+            const float2 a = ra[kk], bb = rb[kk];
+            z = make_float2(a.x + bb.y, bb.x - a.y);
+        }
+        b[k2] = z;
+    });
+}
+
+__device__ __forceinline__ void col_mults(const Geo& g, int kx, int ky, int op, float scale, float2& mx,
+                                          float2& my) {
+    const float kap = scale * g.kappa_t[size_t(kx) * g.ng + ky];
+    mx = g.fx[kx];
+    my = g.fy[ky];
+    if (op == 1) {  // D factor = -conj(G factor)
+        mx.x = -mx.x;
+        my.x = -my.x;
+    }
+    mx = cscale(mx, kap);
+    my = cscale(my, kap);
+}
+
+// ---------------------------------------------------------------------------
+// column pass; mode 0: A -> (MX A, MY A) into (A, B); 1: (A, B) -> (MX A, MY B); 2: MX A + MY B -> A.
+// All global loads (the columns and the multiplier tables) are issued before the first barrier.
+template <int N1, int N2, int CC>
+__global__ void __launch_bounds__(CC * Fft2<N1, N2>::T) kf_col(Geo g, float2* __restrict__ A,
+                                                              float2* __restrict__ B, int mode, int op,
+                                                              float scale) {
+    using F = Fft2<N1, N2>;
+    constexpr int N = F::N;
+    extern __shared__ float2 sm[];
+    float2* tw = sm;                        // [N]
+    float2* MX = tw + N;                    // [N][CC] x multiplier at (ky, c)
+    float2* MY = MX + N * CC;               // [N][CC]
+    float2* Z0 = MY + N * CC;               // transposes, [ZS][CC] each
+    float2* Z1 = Z0 + F::ZS * CC;
+    float2* Z2 = Z1 + F::ZS * CC;
+    float2* Z3 = Z2 + F::ZS * CC;
+    const int k = blockIdx.y;
+    const int c = threadIdx.x % CC, idx = threadIdx.x / CC;
+    const int kx = blockIdx.x * CC + c;
+    const bool colok = kx < g.hc;
+    const int kxc = colok ? kx : g.hc - 1;
+    const bool two = mode != 0;
+    const size_t base = size_t(k) * N * g.hp + kxc;
+    // prologue: tables into shared memory (independent of the preceding kernel) ...
+    constexpr int NT = CC * F::T;
+    static_for<0, (N + NT - 1) / NT>([&](auto I) {
+        const int i = decltype(I)::value * NT + threadIdx.x;
+        if (i < N) tw[i] = g.tw[i];
+    });
+    static_for<0, (N * CC + NT - 1) / NT>([&](auto I) {
+        const int i = decltype(I)::value * NT + threadIdx.x;
+        if (i < N * CC) {
+            const int cc = i % CC, ky = i / CC;
+            const int kxs = min(int(blockIdx.x) * CC + cc, g.hc - 1);
+            float2 mx, my;
+            col_mults(g, kxs, ky, op, scale, mx, my);
+            MX[i] = mx;
+            MY[i] = my;
+        }
+    });
+    // ... then the columns written by the preceding pass (A layout)
+    pdl_wait_then_release();
+    float2 a0[N1], a1[N1];
+    if (idx < N2) {
+        static_for<0, N1>([&](auto I) {
+            constexpr int n1 = decltype(I)::value;
+            a0[n1] = A[base + size_t(N2 * n1 + idx) * g.hp];
+            if (two) a1[n1] = B[base + size_t(N2 * n1 + idx) * g.hp];
+        });
+    }
+    __syncthreads();
+    if (idx < N2) {
+        F::template fwd_a<CC>(a0, idx, Z0 + c, tw);
+        if (two) F::template fwd_a<CC>(a1, idx, Z1 + c, tw);
+    }
+    __syncthreads();
+    if (idx < N1) {
+        float2 b0[N2], b1[N2];
+        F::template fwd_b_load<CC>(b0, idx, Z0 + c);
+        if (two) F::template fwd_b_load<CC>(b1, idx, Z1 + c);
+        F::fwd_b(b0);
+        if (two) F::fwd_b(b1);
+        static_for<0, N2>([&](auto I) {
+            constexpr int k2 = decltype(I)::value;
+            const int m = (idx + N1 * k2) * CC + c;
+            const float2 mx = MX[m], my = MY[m];
+            if (mode == 0) {
+                const float2 X = b0[k2];
+                b0[k2] = cmul(X, mx);
+                b1[k2] = cmul(X, my);
+            } else if (mode == 1) {
+                b0[k2] = cmul(b0[k2], mx);
+                b1[k2] = cmul(b1[k2], my);
+            } else {
+                b0[k2] = cadd(cmul(b0[k2], mx), cmul(b1[k2], my));
+            }
+        });
+        F::template inv_b<CC>(b0, idx, Z2 + c, tw);
+        if (mode != 2) F::template inv_b<CC>(b1, idx, Z3 + c, tw);
+    }
+    __syncthreads();
+    if (idx < N2 && colok) {
+        F::template inv_a_load<CC>(a0, idx, Z2 + c);
+        F::inv_a(a0);
+        if (mode != 2) {
+            F::template inv_a_load<CC>(a1, idx, Z3 + c);
+            F::inv_a(a1);
+        }
+        static_for<0, N1>([&](auto I) {
+            constexpr int n1 = decltype(I)::value;
+            A[base + size_t(idx + N2 * n1) * g.hp] = a0[n1];
+            if (mode != 2) B[base + size_t(idx + N2 * n1) * g.hp] = a1[n1];
+        });
+    }
+}
+
+// Split the natural-order spectra W[j] (of a_j + i b_j) of nseq rows into half spectra:
+// a_j -> row rowa(j), b_j -> row rowb(j).
+template <class F, class RowA, class RowB>
+__device__ __forceinline__ void unpack_rows(const float2* Z, int nseq, RowA rowa, RowB rowb) {
+    constexpr int H = F::N / 2 + 1;
+    for (int i = threadIdx.x; i < nseq * H; i += blockDim.x) {
+        const int j = i / H, kx = i - j * H;
+        const float2* W = Z + j * F::ZS;
+        const float2 zk = W[kx];
+        const float2 zm = W[kx == 0 ? 0 : F::N - kx];
+        rowa(j)[kx] = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
+        rowb(j)[kx] = make_float2(0.5f * (zk.y + zm.y), -0.5f * (zk.x - zm.x));
+    }
+}
+
+// finish the forward transforms whose A-layout halves fwd_a stored in Zs (nseq
+// buffers of ZS): natural-order spectrum into Zs.  Contains two barriers.
+template <class F>
+__device__ __forceinline__ void finish_fwd(float2* Zs, int idx, bool active) {
+    float2 b[F::N2];
+    if (active) F::fwd_b_load(b, idx, Zs);
+    __syncthreads();
+    if (active) {
+        F::fwd_b(b);
+        static_for<0, F::N2>([&](auto I) { Zs[idx + F::N1 * decltype(I)::value] = b[decltype(I)::value]; });
+    }
+    __syncthreads();
+}
+
+// Shared memory of the row passes: twiddles, two transpose buffers of RR rows, RR real rows.
+template <class F, int RR>
+struct RowSmem {
+    static constexpr size_t bytes = (F::N + 2 * RR * F::ZS) * sizeof(float2) + RR * F::N * sizeof(float);
+};
+
+// ---------------------------------------------------------------------------
+// velocity row pass; kind 0 forward: u <- a'(a' u - g) (init: u = g/2 first),
+// kind 1 adjoint: t' = a'(ub + g), ub <- a' t'.  Then (A, B) <- R2C of the new pair.
+template <int N1, int N2, int RR>
+__global__ void __launch_bounds__(RR * Fft2<N1, N2>::T) kf_row_u(Geo g, float2* __restrict__ A,
+                                                                float2* __restrict__ B, float* __restrict__ ux,
+                                                                float* __restrict__ uy, int kind, int init) {
+    using F = Fft2<N1, N2>;
+    constexpr int N = F::N, T = F::T;
+    extern __shared__ float2 sm[];
+    float2* tw = sm;
+    float2* Z0 = sm + N;
+    float2* Z1 = Z0 + RR * F::ZS;
+    const int k = blockIdx.y, y0 = blockIdx.x * RR;
+    const int r = threadIdx.x / T, idx = threadIdx.x % T;
+    const int nr = min(RR, N - y0);
+    const bool rowok = r < nr;
+    const bool bact = rowok && idx < N1, aact = rowok && idx < N2;
+    const size_t row = size_t(k) * N + y0 + min(r, nr - 1);
+    const int yy = y0 + min(r, nr - 1);
+    float* uxr = ux + row * N;
+    float* uyr = uy + row * N;
+    // prologue: state and PML factors (A layout) and twiddles, which the preceding
+    // kernel does not write, then the spectra (B layout) after the dependency wait
+    float sx[N1], sy[N1], fa[N1];
+    if (aact) {
+        static_for<0, N1>([&](auto I) {
+            constexpr int n1 = decltype(I)::value;
+            const int x = idx + N2 * n1;
+            sx[n1] = (kind == 0 && init) ? 0.f : uxr[x];
+            sy[n1] = (kind == 0 && init) ? 0.f : uyr[x];
+            fa[n1] = g.a_stag[x];
+        });
+    }
+    const float ay = g.a_stag[yy];
+    for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = g.tw[i];
+    pdl_wait_then_release();
+    float2 b[N2];
+    if (bact) load_c2r_b<F>(b, idx, A + row * g.hp, B + row * g.hp);
+    __syncthreads();
+    if (bact) F::inv_b(b, idx, Z0 + r * F::ZS, tw);
+    __syncthreads();
+    if (aact) {
+        float2 a[N1];
+        F::inv_a_load(a, idx, Z0 + r * F::ZS);
+        F::inv_a(a);
+        static_for<0, N1>([&](auto I) {
+            constexpr int n1 = decltype(I)::value;
+            const int x = idx + N2 * n1;
+            const float2 gv = a[n1];
+            const float ax = fa[n1];
+            if (kind == 0) {
+                const float uxo = init ? 0.5f * gv.x : sx[n1];
+                const float uyo = init ? 0.5f * gv.y : sy[n1];
+                const float uxn = ax * (ax * uxo - gv.x);
+                const float uyn = ay * (ay * uyo - gv.y);
+                uxr[x] = uxn;
+                uyr[x] = uyn;
+                a[n1] = make_float2(uxn, uyn);
+            } else {
+                const float tpx = ax * (sx[n1] + gv.x);
+                const float tpy = ay * (sy[n1] + gv.y);
+                uxr[x] = ax * tpx;
+                uyr[x] = ay * tpy;
+                a[n1] = make_float2(tpx, tpy);
+            }
+        });
+        F::fwd_a(a, idx, Z1 + r * F::ZS, tw);
+    }
+    __syncthreads();
+    finish_fwd<F>(Z1 + r * F::ZS, idx, bact);
+    unpack_rows<F>(Z1, nr, [&](int j) { return A + (size_t(k) * N + y0 + j) * g.hp; },
+                   [&](int j) { return B + (size_t(k) * N + y0 + j) * g.hp; });
+}
+
+// density / pressure row pass (mode 0 regular, 1 init from p0, 2 restore), sensor gather,
+// history, then A <- R2C of p (two rows per complex transform)
+template <int N1, int N2, int RR>
+__global__ void __launch_bounds__(RR * Fft2<N1, N2>::T) kf_row_rho(Geo g, float2* __restrict__ A,
+                                                                  const float2* __restrict__ B,
+                                                                  float* __restrict__ rx, float* __restrict__ ry,
+                                                                  const float* __restrict__ cg, int mode,
+                                                                  const float* __restrict__ p0,
+                                                                  float* __restrict__ y, int tstep,
+                                                                  float* __restrict__ hist, int hist_slot) {
+    using F = Fft2<N1, N2>;
+    constexpr int N = F::N, T = F::T;
+    extern __shared__ float2 sm[];
+    float2* tw = sm;
+    float2* Z0 = sm + N;
+    float2* Z1 = Z0 + RR * F::ZS;
+    float* P = reinterpret_cast<float*>(Z1 + RR * F::ZS);   // [RR][N]
+    const int k = blockIdx.y, y0 = blockIdx.x * RR;
+    const int r = threadIdx.x / T, idx = threadIdx.x % T;
+    const int nr = min(RR, N - y0);
+    const bool rowok = r < nr;
+    const bool bact = mode == 0 && rowok && idx < N1, aact = rowok && idx < N2;
+    const int yy = y0 + min(r, nr - 1);
+    const size_t row = size_t(k) * N + yy;
+    float* rxr = rx + row * N;
+    float* ryr = ry + row * N;
+    const float* cr = cg + size_t(yy) * N;
+    // prologue: state, medium, PML (written two or more kernels earlier), twiddles
+    float s0[N1], s1[N1], cc[N1], fa[N1];
+    if (aact) {
+        const int yd = yy - g.P;
+        static_for<0, N1>([&](auto I) {
+            constexpr int n1 = decltype(I)::value;
+            const int x = idx + N2 * n1;
+            cc[n1] = cr[x];
+            fa[n1] = g.a_cell[x];
+            if (mode == 1) {
+                const int xd = x - g.P;
+                s0[n1] = (xd >= 0 && xd < g.n && yd >= 0 && yd < g.n) ? p0[(size_t(k) * g.n + yd) * g.n + xd] : 0.f;
+                s1[n1] = 0.f;
+            } else {
+                s0[n1] = rxr[x];
+                s1[n1] = ryr[x];
+            }
+        });
+    }
+    const float acy = g.a_cell[yy];
+    for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = g.tw[i];
+    pdl_wait_then_release();
+    float2 b[N2];
+    if (bact) load_c2r_b<F>(b, idx, A + row * g.hp, B + row * g.hp);
+    __syncthreads();
+    if (bact) F::inv_b(b, idx, Z0 + r * F::ZS, tw);
+    __syncthreads();
+    if (aact) {
+        float* Pr = P + r * N;
+        float* hr = hist ? hist + (size_t(k) * g.s_eff + hist_slot) * N * N + size_t(yy) * N : nullptr;
+        float2 a[N1];
+        if (mode == 0) {
+            F::inv_a_load(a, idx, Z0 + r * F::ZS);
+            F::inv_a(a);
+        }
+        static_for<0, N1>([&](auto I) {
+            constexpr int n1 = decltype(I)::value;
+            const int x = idx + N2 * n1;
+            const float c = cc[n1];
+            float pv;
+            if (mode == 0) {
+                const float2 gv = a[n1];
+                const float acx = fa[n1];
+                const float rxn = acx * (acx * s0[n1] - gv.x);
+                const float ryn = acy * (acy * s1[n1] - gv.y);
+                rxr[x] = rxn;
+                ryr[x] = ryn;
+                pv = c * c * (rxn + ryn);
+            } else if (mode == 1) {
+                pv = s0[n1];
+                const float rv = pv / (2.f * c * c);
+                rxr[x] = rv;
+                ryr[x] = rv;
+            } else {
+                pv = c * c * (s0[n1] + s1[n1]);
+            }
+            Pr[x] = pv;
+            if (hr) hr[x] = pv;
+        });
+    }
+    __syncthreads();
+    if (y) {
+        const int e0 = g.srow[y0], e1 = g.srow[y0 + nr];
+        for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+            const int2 se = g.sent[e];
+            const float4 sw = g.sentw[e];
+            const int rr = int(sw.w) - y0;
+            const float v = sw.z * (sw.x * P[rr * N + se.y] + sw.y * P[rr * N + se.y + 1]);
+            // at most two adds (rows iy, iy+1) onto a zeroed sample: order-independent
+            atomicAdd(&y[(size_t(k) * g.nt + tstep) * g.m + se.x], v);
+        }
+    }
+    const int np = nr / 2;
+    const bool pairok = r < np;
+    if (pairok && idx < N2) {
+        float2 a[N1];
+        static_for<0, N1>([&](auto I) {
+            constexpr int n1 = decltype(I)::value;
+            const int x = N2 * n1 + idx;
+            a[n1] = make_float2(P[(2 * r) * N + x], P[(2 * r + 1) * N + x]);
+        });
+        F::fwd_a(a, idx, Z1 + r * F::ZS, tw);
+    }
+    __syncthreads();
+    finish_fwd<F>(Z1 + r * F::ZS, idx, pairok && idx < N1);
+    unpack_rows<F>(Z1, np, [&](int j) { return A + (size_t(k) * N + y0 + 2 * j) * g.hp; },
+                   [&](int j) { return A + (size_t(k) * N + y0 + 2 * j + 1) * g.hp; });
+}
+
+// adjoint density row pass: pb = C2R(Q) + S^T r^n; rb += c^2 pb; cbar += 2 p pb / c;
+// t = a rb; rb <- a t; (A2, B2) <- R2C(t_x, t_y)
+template <int N1, int N2, int RR>
+__global__ void __launch_bounds__(RR * Fft2<N1, N2>::T) kf_row_adj_rho(Geo g, float2* __restrict__ A2,
+                                                                      float2* __restrict__ B2,
+                                                                      float* __restrict__ rbx,
+                                                                      float* __restrict__ rby,
+                                                                      float* __restrict__ cbar,
+                                                                      const float* __restrict__ cg, int first,
+                                                                      const float* __restrict__ resid, int tstep,
+                                                                      const float* __restrict__ hist,
+                                                                      int hist_slot) {
+    using F = Fft2<N1, N2>;
+    constexpr int N = F::N, T = F::T;
+    extern __shared__ float2 sm[];
+    float2* tw = sm;
+    float2* Z0 = sm + N;
+    float2* Z1 = Z0 + RR * F::ZS;
+    float* PB = reinterpret_cast<float*>(Z1 + RR * F::ZS);   // [RR][N]
+    const int k = blockIdx.y, y0 = blockIdx.x * RR;
+    const int r = threadIdx.x / T, idx = threadIdx.x % T;
+    const int nr = min(RR, N - y0);
+    const bool rowok = r < nr;
+    const int np = nr / 2;
+    const bool pairok = r < np;
+    const bool bact = !first && pairok && idx < N1, aact = rowok && idx < N2;
+    const int yy = y0 + min(r, nr - 1);
+    const size_t row = size_t(k) * N + yy;
+    const int yd = yy - g.P;
+    const bool yin = yd >= 0 && yd < g.n;
+    float* bx = rbx + row * N;
+    float* by = rby + row * N;
+    // prologue: adjoint state, medium, PML, twiddles; after the wait the spectrum and the
+    // pressure history (the segment recompute that writes it may be the preceding kernel)
+    float s0[N1], s1[N1], cc[N1], hv[N1], fa[N1];
+    if (aact) {
+        const float* cr = cg + size_t(yy) * N;
+        static_for<0, N1>([&](auto I) {
+            constexpr int n1 = decltype(I)::value;
+            const int x = idx + N2 * n1;
+            s0[n1] = bx[x];
+            s1[n1] = by[x];
+            cc[n1] = cr[x];
+            fa[n1] = g.a_cell[x];
+        });
+    }
+    const float acy = g.a_cell[yy];
+    for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = g.tw[i];
+    if (first)
+        for (int i = threadIdx.x; i < RR * N; i += blockDim.x) PB[i] = 0.f;
+    pdl_wait_then_release();
+    if (aact) {
+        const float* hr = hist + (size_t(k) * g.s_eff + hist_slot) * N * N + size_t(yy) * N;
+        static_for<0, N1>([&](auto I) { hv[decltype(I)::value] = hr[idx + N2 * decltype(I)::value]; });
+    }
+    float2 b[N2];
+    if (bact) {
+        const float2* q0 = A2 + (size_t(k) * N + y0 + 2 * r) * g.hp;
+        load_c2r_b<F>(b, idx, q0, q0 + g.hp);
+    }
+    __syncthreads();
+    if (bact) F::inv_b(b, idx, Z0 + r * F::ZS, tw);
+    __syncthreads();
+    if (!first && pairok && idx < N2) {
+        float2 a[N1];
+        F::inv_a_load(a, idx, Z0 + r * F::ZS);
+        F::inv_a(a);
+        static_for<0, N1>([&](auto I) {
+            constexpr int n1 = decltype(I)::value;
+            const int x = idx + N2 * n1;
+            PB[(2 * r) * N + x] = a[n1].x;
+            PB[(2 * r + 1) * N + x] = a[n1].y;
+        });
+    }
+    __syncthreads();
+    if (threadIdx.x < nr) {   // S^T r^n, one thread per row: fixed order
+        const int rr = threadIdx.x, yr = y0 + rr;
+        const float* rv = resid + (size_t(k) * g.nt + tstep) * g.m;
+        for (int e = g.srow[yr]; e < g.srow[yr + 1]; ++e) {
+            const int2 se = g.sent[e];
+            const float4 sw = g.sentw[e];
+            const float v = rv[se.x] * sw.z;
+            PB[rr * N + se.y] += sw.x * v;
+            PB[rr * N + se.y + 1] += sw.y * v;
+        }
+    }
+    __syncthreads();
+    if (aact) {
+        float2 a[N1];
+        static_for<0, N1>([&](auto I) {
+            constexpr int n1 = decltype(I)::value;
+            const int x = idx + N2 * n1;
+            const float p_b = PB[r * N + x];
+            const float c = cc[n1];
+            const float c2 = c * c;
+            const float vbx = s0[n1] + c2 * p_b;
+            const float vby = s1[n1] + c2 * p_b;
+            const int xd = x - g.P;
+            if (yin && xd >= 0 && xd < g.n) cbar[(size_t(k) * g.n + yd) * g.n + xd] += 2.f * hv[n1] * p_b / c;
+            const float acx = fa[n1];
+            const float tx = acx * vbx, ty = acy * vby;
+            bx[x] = acx * tx;
+            by[x] = acy * ty;
+            a[n1] = make_float2(tx, ty);
+        });
+        F::fwd_a(a, idx, Z1 + r * F::ZS, tw);
+    }
+    __syncthreads();
+    finish_fwd<F>(Z1 + r * F::ZS, idx, rowok && idx < N1);
+    unpack_rows<F>(Z1, nr, [&](int j) { return A2 + (size_t(k) * N + y0 + j) * g.hp; },
+                   [&](int j) { return B2 + (size_t(k) * N + y0 + j) * g.hp; });
+}
+
+// ---------------------------------------------------------------------------
+// launch with programmatic stream serialisation (the kernel calls pdl_wait_then_release)
+// (pdl = false: an ordinary launch, used after copies and memsets)
+template <typename... KArgs, typename... Args>
+inline void launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st, bool pdl,
+                       Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
+template <int N1, int N2, int RR, int CC>
+struct FixedImpl {
+    using F = Fft2<N1, N2>;
+    static constexpr size_t smem_col = (F::N + 2 * F::N * CC + 4 * F::ZS * CC) * sizeof(float2);
+    static constexpr size_t smem_row = RowSmem<F, RR>::bytes;
+
+    static int configure() {
+        cudaError_t e = cudaFuncSetAttribute((const void*)kf_col<N1, N2, CC>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem_col));
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute((const void*)kf_row_u<N1, N2, RR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     int(smem_row));
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute((const void*)kf_row_rho<N1, N2, RR>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem_row));
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute((const void*)kf_row_adj_rho<N1, N2, RR>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem_row));
+        return e == cudaSuccess ? PAT_OK : cuda_fail(e, "cudaFuncSetAttribute(fixed-size kernels)");
+    }
+    static void col(const Geo& g, cudaStream_t st, float2* A, float2* B, int mode, int op, float scale) {
+        dim3 grid((g.hc + CC - 1) / CC, g.K);
+        launch_pdl(kf_col<N1, N2, CC>, grid, dim3(CC * F::T), smem_col, st, true, g, A, B, mode, op, scale);
+    }
+    static void row_u(const Geo& g, cudaStream_t st, float2* A, float2* B, float* ux, float* uy, int kind,
+                      int init) {
+        dim3 grid((F::N + RR - 1) / RR, g.K);
+        launch_pdl(kf_row_u<N1, N2, RR>, grid, dim3(RR * F::T), smem_row, st, true, g, A, B, ux, uy, kind, init);
+    }
+    static void row_rho(const Geo& g, cudaStream_t st, float2* A, const float2* B, float* rx, float* ry,
+                        const float* cg, int mode, const float* p0, float* y, int tstep, float* hist, int slot) {
+        dim3 grid((F::N + RR - 1) / RR, g.K);
+        launch_pdl(kf_row_rho<N1, N2, RR>, grid, dim3(RR * F::T), smem_row, st, mode == 0, g, A, B, rx, ry, cg, mode, p0, y,
+                   tstep, hist, slot);
+    }
+    static void row_adj_rho(const Geo& g, cudaStream_t st, float2* A2, float2* B2, float* rbx, float* rby,
+                            float* cbar, const float* cg, int first, const float* resid, int tstep,
+                            const float* hist, int slot) {
+        dim3 grid((F::N + RR - 1) / RR, g.K);
+        launch_pdl(kf_row_adj_rho<N1, N2, RR>, grid, dim3(RR * F::T), smem_row, st, true, g, A2, B2, rbx, rby, cbar, cg,
+                   first, resid, tstep, hist, slot);
+    }
+    static FixedOps ops() {
+        return FixedOps{F::N, RR, CC, &configure, &col, &row_u, &row_rho, &row_adj_rho};
+    }
+};
+
+}  // namespace pat

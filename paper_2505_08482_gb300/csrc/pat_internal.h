@@ -12,6 +12,7 @@
 
 namespace pat {
 
+struct FixedOps;
 void set_error(const char* fmt, ...);
 int cuda_fail(cudaError_t e, const char* where);
 
@@ -56,8 +57,10 @@ constexpr int kPartials = 256;
 
 struct pat_plan_s {
     pat_grid g;
-    int n, P, ng, hc, K, nt, m, s, s_eff, nseg;
+    int n, P, ng, hc, hp, K, nt, m, s, s_eff, nseg;   // hp: spectrum row pitch (hc rounded up to 4)
     pat::FftDesc fft;
+    const pat::FixedOps* fast;   // fixed-size passes for this grid side (nullptr: generic Stockham)
+    int variant;       // -1 generic, else index of the fixed-size tile variant
     int R;             // rows per CTA in row passes (even)
     int C;             // spectral columns per CTA in column passes
     size_t smem_row, smem_col;
@@ -89,6 +92,7 @@ struct Launch {
 };
 
 int configure_kernels(pat_plan_s* p);
+int select_variant(pat_plan_s* p, int variant);
 
 // forward
 int launch_medium(const Launch& L, const float* c_dom, float* cg);

@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "pat_internal.h"
+#include "kfixed.cuh"
 
 namespace pat {
 
@@ -101,7 +102,7 @@ Ws resolve(const pat_plan_s* p, void* base, bool grad) {
 
 static void layout(pat_plan_s* p) {
     const size_t f = size_t(p->K) * p->ng * p->ng * sizeof(float);
-    const size_t spec = size_t(p->K) * p->ng * p->hc * sizeof(float2);
+    const size_t spec = size_t(p->K) * p->ng * p->hp * sizeof(float2);
     size_t o = 0;
     p->o_state = o; o = align256(o + 4 * f);
     p->o_cg = o; o = align256(o + size_t(p->ng) * p->ng * sizeof(float));
@@ -138,6 +139,19 @@ extern "C" int pat_pml_auto(int n, int min_pml) {
 
 extern "C" int pat_plan_ng(pat_plan plan) { return plan ? plan->ng : -1; }
 
+extern "C" int pat_plan_variants(pat_plan plan) { return plan ? fixed_variants(plan->ng) : -1; }
+
+extern "C" int pat_plan_set_variant(pat_plan plan, int variant) {
+    if (!plan) { set_error("pat_plan_set_variant: null plan"); return PAT_EINVAL; }
+    if (variant >= fixed_variants(plan->ng)) {
+        set_error("pat_plan_set_variant: grid side %d has %d fixed-size variants", plan->ng, fixed_variants(plan->ng));
+        return PAT_EINVAL;
+    }
+    return select_variant(plan, variant < 0 ? -1 : variant);
+}
+
+extern "C" int pat_plan_variant(pat_plan plan) { return plan ? plan->variant : -2; }
+
 extern "C" int pat_plan_create(pat_plan* out, const pat_grid* g, int m, const double* xy, int K,
                                int ckpt_every) {
     if (!out || !g) { set_error("pat_plan_create: null argument"); return PAT_EINVAL; }
@@ -162,6 +176,7 @@ extern "C" int pat_plan_create(pat_plan* out, const pat_grid* g, int m, const do
     p->P = g->pml;
     p->ng = ng;
     p->hc = ng / 2 + 1;
+    p->hp = (p->hc + 3) & ~3;
     p->K = K;
     p->nt = g->nt;
     p->m = m;

@@ -12,6 +12,9 @@ namespace {
 struct Timing {
     int cls = 0;
     int used = 0;
+    int every = 1;    // time every n-th launch of the class
+    long long seen = 0;
+    bool open = false;
     std::vector<cudaEvent_t> t0, t1;
 };
 Timing g_t;
@@ -22,13 +25,16 @@ void count_launch() { ++g_launches; }
 
 void prof_begin(int cls, cudaStream_t st) {
     ++g_launches;
-    if (g_t.cls == cls && g_t.used < int(g_t.t0.size())) cudaEventRecord(g_t.t0[g_t.used], st);
+    if (g_t.cls != cls) return;
+    g_t.open = (g_t.seen++ % g_t.every) == 0 && g_t.used < int(g_t.t0.size());
+    if (g_t.open) cudaEventRecord(g_t.t0[g_t.used], st);
 }
 
 void prof_end(int cls, cudaStream_t st) {
-    if (g_t.cls == cls && g_t.used < int(g_t.t0.size())) {
+    if (g_t.cls == cls && g_t.open) {
         cudaEventRecord(g_t.t1[g_t.used], st);
         ++g_t.used;
+        g_t.open = false;
     }
 }
 
@@ -38,13 +44,16 @@ using namespace pat;
 
 extern "C" unsigned long long pat_kernel_launches(void) { return g_launches; }
 
-extern "C" int pat_timing_enable(int cls, int max_launches) {
+extern "C" int pat_timing_enable(int cls, int max_launches, int every) {
     for (cudaEvent_t e : g_t.t0) cudaEventDestroy(e);
     for (cudaEvent_t e : g_t.t1) cudaEventDestroy(e);
     g_t.t0.clear();
     g_t.t1.clear();
     g_t.used = 0;
     g_t.cls = 0;
+    g_t.seen = 0;
+    g_t.open = false;
+    g_t.every = every < 1 ? 1 : every;
     if (cls <= 0 || max_launches <= 0) return PAT_OK;
     if (cls > PAT_K_LAST) { set_error("pat_timing_enable: unknown kernel class %d", cls); return PAT_EINVAL; }
     g_t.t0.resize(max_launches);

@@ -93,6 +93,20 @@ class Plan:
     def ng(self):
         return int(B.lib().pat_plan_ng(self._h))
 
+    @property
+    def variants(self) -> int:
+        """Number of fixed-size kernel variants for this grid side (0: generic only)."""
+        return int(B.lib().pat_plan_variants(self._h))
+
+    @property
+    def variant(self) -> int:
+        return int(B.lib().pat_plan_variant(self._h))
+
+    @variant.setter
+    def variant(self, v: int):
+        with torch.cuda.device(self.device):
+            B.check(B.lib().pat_plan_set_variant(self._h, int(v)), "pat_plan_set_variant")
+
     def workspace_bytes(self, kind: int = B.PAT_WS_GRADIENT) -> int:
         return int(B.lib().pat_workspace_bytes(self._h, kind))
 
