@@ -78,6 +78,11 @@ def parse():
     ap.add_argument("--ckpt", type=int, default=WL["ckpt_every"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-steps", type=int, default=0, help="oracle sample length (0 = auto)")
+    ap.add_argument("--batch", action="store_true",
+                    help="batched sweep: 64 reconstructions of uneven size and K, grouped by grid side")
+    ap.add_argument("--batch-instances", type=int, default=64)
+    ap.add_argument("--batch-iters", type=int, default=2)
+    ap.add_argument("--batch-plain", type=int, default=64, help="instances also solved one by one")
     return ap.parse_args()
 
 
@@ -390,6 +395,118 @@ def run_ours(args, rank, world, local_rank):
         print(json.dumps(line), flush=True)
 
 
+def run_batch(args):
+    """Batched serving-style sweep (two-level multigrid N/2 -> N per instance)."""
+    import threading
+
+    import numpy as np
+    import torch
+
+    import pat_synth as ps
+    import paper_2505_08482_gb300 as pkg
+    from paper_2505_08482_gb300 import _binding as B
+    from paper_2505_08482_gb300.solver import GridSpec, Plan, ReconConfig, reconstruct, reconstruct_batched
+    pkg.build()
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    rng = ps.rng_for(2024)
+    sides = [96, 128, 160, 192, 256]
+    specs = [(int(rng.choice(sides)), int(rng.choice([1, 2, 4, 8]))) for _ in range(args.batch_instances)]
+    dx, c_hi = 1e-4, 1750.0
+    f32 = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float32, device=dev)
+    groups = {}
+    for i, (n, K) in enumerate(specs):
+        groups.setdefault(n, []).append((i, K))
+    data = {}
+    cell_steps = 0.0
+    for n, members in groups.items():
+        M, nt = 2 * n, 7 * n
+        P = pml_auto(n)
+        gs = GridSpec(n=n, pml=P, dx=dx, dt=0.3 * dx / c_hi, nt=nt, c_ref=c_hi)
+        xy = ps.circle_sensors(n, M, dx)
+        Ks = [K for _, K in members]
+        gen = Plan(gs, xy, Ks, ckpt_every=32, device=dev)
+        cs, p0s = [], []
+        for i, K in members:
+            r = ps.rng_for(3000 + i)
+            cs.append(ps.ellipse_phantom(n, int(r.integers(2, 9)), r))
+            p0s.append(np.stack([ps.vessel_p0(n, r) for _ in range(K)]))
+        y = gen.forward(f32(np.stack(cs)), f32(np.concatenate(p0s))).cpu().numpy()
+        del gen
+        k0 = 0
+        for (i, K), c in zip(members, cs):
+            yk = ps.add_noise(y[k0:k0 + K], ps.rng_for(4000 + i))
+            data[i] = dict(y_meas=f32(yk), w=f32(ps.noise_weights(yk)),
+                           c_init=f32(np.full((n, n), 0.5 * (c.min() + c.max()))), c_true=c)
+            k0 += K
+        data[("cfg", n)] = ReconConfig(levels=(n // 2, n), L=n * dx, dt_data=gs.dt, nt_data=nt, sensors_xy=xy, K=1,
+                                       iters=args.batch_iters, mem=20, ckpt_every=32, autotune=True)
+    torch.cuda.synchronize()
+    # batched: one call per grid side, the sides concurrently on their own streams
+    lat = {}
+    launches0 = B.lib().pat_kernel_launches()
+    errors = []
+
+    def group_run(n, members):
+        try:
+            stream = torch.cuda.Stream(device=dev)
+            with torch.cuda.stream(stream):
+                res, ms = reconstruct_batched(data[("cfg", n)], [data[i] for i, _ in members], stream=stream)
+            for (i, _), r in zip(members, res):
+                lat[i] = ms
+                data[i]["rows"] = r[2]
+        except Exception as e:  # reported below
+            errors.append(repr(e))
+
+    t0 = time.perf_counter()
+    th = [threading.Thread(target=group_run, args=(n, m)) for n, m in groups.items()]
+    for t in th:
+        t.start()
+    for t in th:
+        t.join()
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    if errors:
+        raise RuntimeError(errors[0])
+    batched_launches = int(B.lib().pat_kernel_launches() - launches0)
+    # forward-equivalent cell-steps: every trial = 1 forward, every gradient = 3
+    for n, members in groups.items():
+        for i, K in members:
+            for r in data[i]["rows"]:
+                lvl_n = n // 2 if r["level"] == 0 else n
+                ng = lvl_n + 2 * pml_auto(lvl_n)
+                nt_l = int(round((7 * n - 1) * (lvl_n / n))) + 1
+                cell_steps += ng * ng * K * (nt_l - 1) * (r["trials"] + 3)
+    # plain GPU: the same instances one at a time, no batching, no graphs, default variant
+    plain = {}
+    tp0 = time.perf_counter()
+    for n, members in groups.items():
+        for i, K in members[: max(1, args.batch_plain * len(members) // len(specs))]:
+            cfg = data[("cfg", n)]
+            cfg.K = K
+            cfg.autotune = False
+            t1 = time.perf_counter()
+            reconstruct(cfg, data[i]["y_meas"], data[i]["w"], data[i]["c_init"])
+            torch.cuda.synchronize()
+            plain[i] = (time.perf_counter() - t1) * 1e3
+    plain_wall = time.perf_counter() - tp0
+    lats = sorted(lat.values())
+    pl = sorted(plain.values())
+    q = lambda v, f: float(np.percentile(v, f)) if v else None
+    frac = len(plain) / len(specs)
+    line = {"metric": "batched sweep aggregate Gcell-steps/s", "value": cell_steps / wall / 1e9,
+            "unit": "Gcell-steps/s", "n_gpus": 1, "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"{len(specs)} reconstructions, N~U{{96..256}}, K~U{{1,2,4,8}}, M=2N, Nt=7N, "
+                                   f"levels N/2->N, {args.batch_iters} L-BFGS iterations per level",
+                       "groups": {str(n): len(m) for n, m in groups.items()}},
+            "wall_s": wall, "latency_ms_p50": q(lats, 50), "latency_ms_p99": q(lats, 99),
+            "plain_wall_s_scaled": plain_wall / frac if frac > 0 else None,
+            "plain_latency_ms_p50": q(pl, 50), "plain_latency_ms_p99": q(pl, 99),
+            "plain_instances_timed": len(plain), "gpu_launches": batched_launches,
+            "speedup_vs_plain": (plain_wall / frac) / wall if frac > 0 else None}
+    print(json.dumps(line), flush=True)
+
+
 def ctypes_read(L):
     import ctypes
     tot = ctypes.c_double(0.0)
@@ -407,6 +524,9 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         run_reference(args, rank)
+        return
+    if args.batch:
+        run_batch(args)
         return
     if world > 1:
         import torch

@@ -87,7 +87,20 @@ typedef struct pat_plan_s* pat_plan;
  * pat_plan_destroy (NULL is accepted). */
 int pat_plan_create(pat_plan* out, const pat_grid* grid, int m, const double* h_sensor_xy,
                     int K, int ckpt_every);
+
+/* A plan for ninst independent reconstructions that share one grid and one
+ * sensor set (a batch: one launch per pass serves all of them).  Instance i
+ * has h_K[i] >= 1 data sets; the K = sum h_K[i] data sets are numbered
+ * instance by instance.  In every call of such a plan the speed of sound
+ * d_c and its gradient d_grad_c are [ninst][N][N], J is [ninst], and p0,
+ * traces, weights and dJ/dp0 are indexed by data set as usual.
+ * pat_plan_create(..., K, ...) is the one-instance case. */
+int pat_plan_create_batched(pat_plan* out, const pat_grid* grid, int m, const double* h_sensor_xy, int ninst,
+                            const int* h_K, int ckpt_every);
 void pat_plan_destroy(pat_plan plan);
+
+/* Number of instances and of data sets (all instances) of a plan. */
+int pat_plan_shape(pat_plan plan, int* ninst, int* K);
 
 /* FFT grid side Ng and PML width of a plan (for callers that size buffers). */
 int pat_plan_ng(pat_plan plan);
@@ -103,6 +116,22 @@ int pat_plan_ng(pat_plan plan);
 int pat_plan_variants(pat_plan plan);
 int pat_plan_set_variant(pat_plan plan, int variant);
 int pat_plan_variant(pat_plan plan);
+
+/* CUDA graphs: with enable != 0, the first pat_forward / pat_adjoint_grad
+ * (or objective evaluation of pat_reconstruct) on a non-default stream with
+ * a given set of buffers and kernel variant is captured into a CUDA graph and
+ * every later call with the same buffers replays it (one launch for the
+ * whole call).  Buffers are keyed by address: a caller that reuses
+ * addresses for new data gets the new data.  enable = 0 frees the graphs. */
+int pat_plan_set_graphs(pat_plan plan, int enable);
+
+/* Autotuner: times a short run of forward steps with every variant of the
+ * plan (generic and fixed-size tile shapes) on this GPU and keeps the
+ * fastest.  d_ws: a forward workspace (NULL: a temporary one is allocated
+ * and freed on the stream).  h_ms: host array of pat_plan_variants(plan)+1
+ * entries (may be NULL) receiving the time per step of variants -1, 0, ...
+ * in ms.  Synchronises the stream; with no fixed-size variant it selects -1. */
+int pat_plan_autotune(pat_plan plan, void* d_ws, size_t ws_bytes, double* h_ms, void* stream);
 
 /* Smallest PML width >= min_pml for which n + 2 P satisfies the grid rules
  * above (Sec. 4.1.1: PML sized so the grid has small prime factors);
@@ -148,7 +177,7 @@ int pat_forward_noalloc(pat_plan plan, const float* d_c, const float* d_p0, floa
  *   J = sum_k w_k/2 || y_pred_k - y_meas_k ||^2,
  *   d_grad_p0 [K][N][N] = dJ/dp0_k,  d_grad_c [N][N] = dJ/dc summed over k.
  * d_w: device [K] float weights w_k = 1/sigma_k^2 (L_e^T L_e = w_k I).
- * d_J: device double (may be NULL) receives J.  d_y_pred: device
+ * d_J: device double[ninst] (may be NULL) receives J per instance.  d_y_pred: device
  * [K][nt][m] (may be NULL) receives the predicted traces.  The workspace
  * must hold PAT_WS_GRADIENT bytes.  Returns PAT_ENONFINITE only through
  * *d_flag semantics of pat_status (the call itself stays asynchronous). */
@@ -206,6 +235,7 @@ typedef struct {
     double alpha0;
     double c1;
     double sigma_p0;
+    int autotune;   /* nonzero: run pat_plan_autotune on every level's plan */
 } pat_recon_cfg;
 
 /* One row per L-BFGS iteration. */
@@ -264,6 +294,29 @@ int pat_timing_enable(int cls, int max_launches, int every);
 /* Sum of the recorded launch durations (ms) and their count; waits for the
  * last recorded event and resets the counter. */
 int pat_timing_read(double* total_ms, long long* launches);
+
+/* One instance of a batched reconstruction: its data d_y_meas
+ * [K][nt_data][m], weights d_w [K], finest-level c (in: initial guess, out:
+ * result) d_c_io [N][N] and p0 d_p0_io [K][N][N] (same semantics), and an
+ * optional report. */
+typedef struct {
+    const float* d_y_meas;
+    const float* d_w;
+    float* d_c_io;
+    float* d_p0_io;
+    int K;
+    pat_report* report;
+} pat_instance;
+
+/* Several independent reconstructions that share cfg (levels, domain,
+ * sensors, time grid, bounds, optimiser settings; cfg->K is ignored), solved
+ * together: every objective or gradient evaluation is one batched solve over
+ * all instances (a plan from pat_plan_create_batched per level), each
+ * instance keeps its own L-BFGS state and FP64 line search, and the
+ * instances advance in lockstep (an instance that has converged or failed
+ * keeps its point).  Results are those of pat_reconstruct on each instance
+ * alone.  Synchronises the stream once per evaluation round. */
+int pat_reconstruct_batched(const pat_recon_cfg* cfg, int ninst, const pat_instance* inst, void* stream);
 
 /* Message describing the last error on the calling thread. */
 const char* pat_last_error(void);

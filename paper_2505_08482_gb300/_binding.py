@@ -44,7 +44,12 @@ class PatReconCfg(ctypes.Structure):
                 ("cfl", c_double), ("c_lo", c_double), ("c_hi", c_double), ("p0_lo", c_double),
                 ("c_bg", c_double), ("rho0", c_double), ("pml_alpha", c_double), ("min_pml", c_int),
                 ("mem", c_int), ("iters", c_int), ("max_halvings", c_int), ("ckpt_every", c_int),
-                ("rtol", c_double), ("alpha0", c_double), ("c1", c_double), ("sigma_p0", c_double)]
+                ("rtol", c_double), ("alpha0", c_double), ("c1", c_double), ("sigma_p0", c_double),
+                ("autotune", c_int)]
+
+
+class PatInstance(ctypes.Structure):
+    pass
 
 
 class PatIterReport(ctypes.Structure):
@@ -57,10 +62,16 @@ class PatReport(ctypes.Structure):
                 ("total_ms", c_double)]
 
 
+PatInstance._fields_ = [("d_y_meas", c_void_p), ("d_w", c_void_p), ("d_c_io", c_void_p), ("d_p0_io", c_void_p),
+                        ("K", c_int), ("report", POINTER(PatReport))]
+
 # name -> (restype, argtypes)
 SIGNATURES = {
     "pat_plan_create": (c_int, [POINTER(c_void_p), POINTER(PatGrid), c_int, POINTER(c_double), c_int, c_int]),
+    "pat_plan_create_batched": (c_int, [POINTER(c_void_p), POINTER(PatGrid), c_int, POINTER(c_double), c_int,
+                                        POINTER(c_int), c_int]),
     "pat_plan_destroy": (None, [c_void_p]),
+    "pat_plan_shape": (c_int, [c_void_p, POINTER(c_int), POINTER(c_int)]),
     "pat_plan_ng": (c_int, [c_void_p]),
     "pat_plan_variants": (c_int, [c_void_p]),
     "pat_plan_set_variant": (c_int, [c_void_p, c_int]),
@@ -75,6 +86,9 @@ SIGNATURES = {
     "pat_status": (c_int, [c_void_p, c_void_p, POINTER(c_int), c_void_p]),
     "pat_reconstruct": (c_int, [POINTER(PatReconCfg), c_void_p, c_void_p, c_void_p, c_void_p, POINTER(PatReport),
                                 c_void_p]),
+    "pat_reconstruct_batched": (c_int, [POINTER(PatReconCfg), c_int, POINTER(PatInstance), c_void_p]),
+    "pat_plan_set_graphs": (c_int, [c_void_p, c_int]),
+    "pat_plan_autotune": (c_int, [c_void_p, c_void_p, c_size_t, POINTER(c_double), c_void_p]),
     "pat_kernel_launches": (ctypes.c_ulonglong, []),
     "pat_timing_enable": (c_int, [c_int, c_int, c_int]),
     "pat_timing_read": (c_int, [POINTER(c_double), POINTER(ctypes.c_longlong)]),

@@ -106,6 +106,38 @@ int reverse_sweep(pat_plan_s* p, const float* p0, const float* r, float* grad_p0
     return PAT_OK;
 }
 
+// Run body() directly, or (graphs enabled, non-default stream) replay the graph
+// captured from the first call with the same kind, buffers and kernel variant.
+template <class F>
+int with_graph(pat_plan_s* p, int kind, const std::array<const void*, 10>& key, size_t ws_bytes, cudaStream_t st,
+               F&& body) {
+    if (!p->use_graphs || st == nullptr) return body();
+    for (auto& g : p->graphs)
+        if (g.kind == kind && g.variant == p->variant && g.key == key && g.ws_bytes == ws_bytes) {
+            PAT_CUDA(cudaGraphLaunch(g.exec, st));
+            add_launches(g.launches);
+            return PAT_OK;
+        }
+    const unsigned long long l0 = launches_so_far();
+    PAT_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    int rc = body();
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(st, &graph);
+    if (rc != PAT_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return rc;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+    cudaGraphExec_t exec = nullptr;
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+    const unsigned long long n = launches_so_far() - l0;
+    p->graphs.push_back(pat_plan_s::Graph{kind, p->variant, key, ws_bytes, exec, n});
+    PAT_CUDA(cudaGraphLaunch(exec, st));
+    return PAT_OK;
+}
+
 int check_ws(const pat_plan_s* p, const void* ws, size_t bytes, bool grad) {
     if (!ws) { set_error("workspace is NULL"); return PAT_EINVAL; }
     if (reinterpret_cast<uintptr_t>(ws) % 256 != 0) { set_error("workspace must be 256-byte aligned"); return PAT_EINVAL; }
@@ -123,10 +155,13 @@ int pat::objective(pat_plan_s* p, const float* c, const float* p0, const float* 
                    double* J_dev, void* ws, size_t ws_bytes, cudaStream_t st) {
     RC(check_ws(p, ws, ws_bytes, true));
     Ws w = resolve(p, ws, true);
-    RC(forward_sweep(p, c, p0, w.ypred, w, false, st));
-    Launch L{p, st};
-    RC(launch_residual(L, w, w.ypred, ymeas, wts, w.resid, w.J));
-    if (J_dev) PAT_CUDA(cudaMemcpyAsync(J_dev, w.J, sizeof(double), cudaMemcpyDeviceToDevice, st));
+    RC(with_graph(p, 0, {c, p0, ymeas, wts, J_dev, ws}, ws_bytes, st, [&]() -> int {
+        RC(forward_sweep(p, c, p0, w.ypred, w, false, st));
+        Launch L{p, st};
+        RC(launch_residual(L, w, w.ypred, ymeas, wts, w.resid, w.J));
+        if (J_dev) PAT_CUDA(cudaMemcpyAsync(J_dev, w.J, p->ninst * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        return PAT_OK;
+    }));
     p->hist_valid_ws = nullptr;
     return PAT_OK;
 }
@@ -138,7 +173,8 @@ extern "C" int pat_forward(pat_plan p, const float* c, const float* p0, float* y
     const bool keep = ws_bytes >= p->ws_grad;
     Ws w = resolve(p, ws, keep);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    RC(forward_sweep(p, c, p0, y, w, keep, st));
+    RC(with_graph(p, keep ? 2 : 1, {c, p0, y, ws}, ws_bytes, st,
+                  [&]() -> int { return forward_sweep(p, c, p0, y, w, keep, st); }));
     p->hist_valid_ws = keep ? ws : nullptr;
     return PAT_OK;
 }
@@ -154,11 +190,13 @@ extern "C" int pat_adjoint_grad(pat_plan p, const float* c, const float* p0, con
     Ws w = resolve(p, ws, true);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     float* yp = y_pred ? y_pred : w.ypred;
-    RC(forward_sweep(p, c, p0, yp, w, true, st));
-    Launch L{p, st};
-    RC(launch_residual(L, w, yp, y_meas, wts, w.resid, w.J));
-    if (J) PAT_CUDA(cudaMemcpyAsync(J, w.J, sizeof(double), cudaMemcpyDeviceToDevice, st));
-    RC(reverse_sweep(p, p0, w.resid, grad_p0, grad_c, w, true, st));
+    RC(with_graph(p, 3, {c, p0, y_meas, wts, grad_p0, grad_c, J, y_pred, ws}, ws_bytes, st, [&]() -> int {
+        RC(forward_sweep(p, c, p0, yp, w, true, st));
+        Launch L{p, st};
+        RC(launch_residual(L, w, yp, y_meas, wts, w.resid, w.J));
+        if (J) PAT_CUDA(cudaMemcpyAsync(J, w.J, p->ninst * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        return reverse_sweep(p, p0, w.resid, grad_p0, grad_c, w, true, st);
+    }));
     p->hist_valid_ws = nullptr;
     return PAT_OK;
 }
@@ -175,6 +213,57 @@ extern "C" int pat_vjp(pat_plan p, const float* c, const float* p0, const float*
     RC(reverse_sweep(p, p0, ybar, grad_p0, grad_c, w, valid, st));
     p->hist_valid_ws = nullptr;
     return PAT_OK;
+}
+
+extern "C" int pat_plan_autotune(pat_plan p, void* ws, size_t ws_bytes, double* h_ms, void* stream) {
+    if (!p) { set_error("pat_plan_autotune: null plan"); return PAT_EINVAL; }
+    const int nv = pat_plan_variants(p);
+    if (nv <= 0) return select_variant(p, -1);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    void* own = nullptr;
+    if (!ws) {
+        PAT_CUDA(cudaMallocAsync(&own, p->ws_fwd, st));
+        ws = own;
+        ws_bytes = p->ws_fwd;
+    }
+    int rc = check_ws(p, ws, ws_bytes, false);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    double best = 1e300;
+    int bestv = -1;
+    if (rc == PAT_OK) {
+        // zero state and spectra; the timed steps then run on finite values
+        if (cudaMemsetAsync(ws, 0, p->ws_fwd, st) != cudaSuccess || cudaEventCreate(&e0) != cudaSuccess ||
+            cudaEventCreate(&e1) != cudaSuccess)
+            rc = cuda_fail(cudaGetLastError(), "pat_plan_autotune");
+    }
+    Ws w = resolve(p, ws, false);
+    Launch L{p, st};
+    const int nsteps = 12;
+    for (int v = -1; v < nv && rc == PAT_OK; ++v) {
+        rc = select_variant(p, v);
+        for (int n = 1; n < 4 && rc == PAT_OK; ++n) rc = step(L, w, n, nullptr, nullptr, 0);
+        if (rc != PAT_OK) break;
+        cudaEventRecord(e0, st);
+        for (int n = 1; n <= nsteps && rc == PAT_OK; ++n) rc = step(L, w, n, nullptr, nullptr, 0);
+        cudaEventRecord(e1, st);
+        if (rc != PAT_OK) break;
+        float ms = 0.f;
+        if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+            rc = cuda_fail(cudaGetLastError(), "pat_plan_autotune timing");
+            break;
+        }
+        const double per = double(ms) / nsteps;
+        if (h_ms) h_ms[v + 1] = per;
+        if (per < best) {
+            best = per;
+            bestv = v;
+        }
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (own) cudaFreeAsync(own, st);
+    if (rc != PAT_OK) return rc;
+    return select_variant(p, bestv);
 }
 
 extern "C" int pat_status(pat_plan p, const void* ws, int* h_flag, void* stream) {

@@ -21,6 +21,7 @@ struct Geo {
     const int* srow;
     const int2* sent;
     const float4* sentw;
+    const int* kinst;    // instance of each data set (selects its c)
 };
 
 inline Geo geo(const pat_plan_s* p) {
@@ -31,6 +32,7 @@ inline Geo geo(const pat_plan_s* p) {
     g.tw = p->t.tw; g.kappa_t = p->t.kappa_t; g.fx = p->t.fx; g.fy = p->t.fy;
     g.a_cell = p->t.a_cell; g.a_stag = p->t.a_stag;
     g.srow = p->t.srow; g.sent = p->t.sent; g.sentw = p->t.sentw;
+    g.kinst = p->t.kinst;
     return g;
 }
 
@@ -42,6 +44,11 @@ inline Geo geo(const pat_plan_s* p) {
 __device__ __forceinline__ void pdl_wait_then_release() {
     asm volatile("griddepcontrol.wait;" ::: "memory");
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+// c of data set k's instance on the grid
+__device__ __forceinline__ const float* medium_of(const Geo& g, const float* cg, int k) {
+    return cg + size_t(g.kinst[k]) * g.ng * g.ng;
 }
 
 __device__ __forceinline__ void load_twiddles(float2* tw, const Geo& g) {

@@ -14,7 +14,9 @@
 // k-space multipliers of the column pass.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
+#include <mutex>
 
 #include "pat_internal.h"
 #include "geo.cuh"
@@ -43,6 +45,7 @@ __global__ void __launch_bounds__(256) k_row_rho(Geo g, float2* __restrict__ A, 
     float2* w = z + R * ng;
     load_twiddles(tw, g);
     const size_t kf = size_t(k) * ng * ng;
+    cg = medium_of(g, cg, k);
     float* pr;
     float2* freeb;
     if (mode == 0) {
@@ -306,6 +309,7 @@ __global__ void __launch_bounds__(256) k_row_adj_rho(Geo g, float2* __restrict__
     }
     scatter_rows(g, pb, resid, k, tstep, y0, nr);
     const size_t kf = size_t(k) * ng * ng;
+    cg = medium_of(g, cg, k);
     const float* hp = hist + (size_t(k) * g.s_eff + hist_slot) * ng * ng;
     for (int i = threadIdx.x; i < nr * ng; i += blockDim.x) {
         const int r = i / ng, x = i - r * ng, yy = y0 + r;
@@ -447,6 +451,7 @@ __global__ void __launch_bounds__(256) k_row_adj_final2(Geo g, const float2* __r
     float* q;
     c2r_rows(g, A2, k, y0, nr, z, w, tw, q);
     const size_t kf = size_t(k) * ng * ng;
+    cg = medium_of(g, cg, k);
     for (int i = threadIdx.x; i < nr * ng; i += blockDim.x) {
         const int r = i / ng, x = i - r * ng, yy = y0 + r;
         const int xd = x - g.P, yd = yy - g.P;
@@ -461,39 +466,48 @@ __global__ void __launch_bounds__(256) k_row_adj_final2(Geo g, const float2* __r
     }
 }
 
-// grad_c = sum_k cbar_k (fixed order)
-__global__ void k_reduce_cbar(const float* __restrict__ cbar, float* __restrict__ gc, int K, int nn) {
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nn; i += gridDim.x * blockDim.x) {
+// grad_c of each instance = sum of cbar_k over its data sets (fixed order)
+__global__ void k_reduce_cbar(const float* __restrict__ cbar, float* __restrict__ gc, const int* __restrict__ kfirst,
+                              int ninst, int nn) {
+    const size_t total = size_t(ninst) * nn;
+    for (size_t t = size_t(blockIdx.x) * blockDim.x + threadIdx.x; t < total; t += size_t(gridDim.x) * blockDim.x) {
+        const int inst = int(t / nn);
+        const size_t i = t - size_t(inst) * nn;
         float s = 0.f;
-        for (int k = 0; k < K; ++k) s += cbar[size_t(k) * nn + i];
-        gc[i] = s;
+        for (int k = kfirst[inst]; k < kfirst[inst + 1]; ++k) s += cbar[size_t(k) * nn + i];
+        gc[t] = s;
     }
 }
 
-// c on the whole grid: c_dom inside the domain, c_bg in the PML
-__global__ void k_medium(const float* __restrict__ cd, float* __restrict__ cg, int n, int P, int ng, float cbg) {
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ng * ng; i += gridDim.x * blockDim.x) {
+// c on the whole grid of every instance: c_dom inside the domain, c_bg in the PML
+__global__ void k_medium(const float* __restrict__ cd, float* __restrict__ cg, int n, int P, int ng, int ninst,
+                         float cbg) {
+    const size_t total = size_t(ninst) * ng * ng;
+    for (size_t t = size_t(blockIdx.x) * blockDim.x + threadIdx.x; t < total; t += size_t(gridDim.x) * blockDim.x) {
+        const int inst = int(t / (size_t(ng) * ng));
+        const int i = int(t - size_t(inst) * ng * ng);
         const int yy = i / ng, x = i - yy * ng;
         const int xd = x - P, yd = yy - P;
-        cg[i] = (xd >= 0 && xd < n && yd >= 0 && yd < n) ? cd[size_t(yd) * n + xd] : cbg;
+        cg[t] = (xd >= 0 && xd < n && yd >= 0 && yd < n) ? cd[(size_t(inst) * n + yd) * n + xd] : cbg;
     }
 }
 
-// r = w_k (y_pred - y_meas); per-block FP64 partial sums of w_k/2 (y_pred - y_meas)^2
+// r = w_k (y_pred - y_meas); FP64 partial sums of w_k/2 (y_pred - y_meas)^2, kResidBlocks per
+// data set (block (b, k) covers the samples b, b + kResidBlocks * 256, ... of data set k)
 __global__ void __launch_bounds__(256) k_residual(const float* __restrict__ yp, const float* __restrict__ ym,
                                                   const float* __restrict__ wts, float* __restrict__ r,
-                                                  int K, int ntm, double* __restrict__ part, int* __restrict__ flag) {
+                                                  int ntm, double* __restrict__ part, int* __restrict__ flag) {
     __shared__ double red[256];
+    const int k = blockIdx.y;
+    const size_t off = size_t(k) * ntm;
+    const float wk = wts[k];
     double acc = 0.0;
-    int bad = 0;
-    const size_t total = size_t(K) * ntm;
-    for (size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x; i < total; i += size_t(gridDim.x) * blockDim.x) {
-        const int k = int(i / ntm);
-        const float d = yp[i] - ym[i];
-        const float wk = wts[k];
-        r[i] = wk * d;
+    int bad = !isfinite(wk);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ntm; i += gridDim.x * blockDim.x) {
+        const float d = yp[off + i] - ym[off + i];
+        r[off + i] = wk * d;
         acc += 0.5 * double(wk) * double(d) * double(d);
-        if (!isfinite(d) || !isfinite(wk)) bad = 1;
+        if (!isfinite(d)) bad = 1;
     }
     red[threadIdx.x] = acc;
     __syncthreads();
@@ -501,16 +515,17 @@ __global__ void __launch_bounds__(256) k_residual(const float* __restrict__ yp, 
         if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
         __syncthreads();
     }
-    if (threadIdx.x == 0) part[blockIdx.x] = red[0];
+    if (threadIdx.x == 0) part[size_t(k) * gridDim.x + blockIdx.x] = red[0];
     if (bad) atomicOr(flag, 1);
 }
 
-__global__ void k_sum_partials(const double* __restrict__ part, int np, double* __restrict__ J,
-                               int* __restrict__ flag) {
-    if (threadIdx.x == 0 && blockIdx.x == 0) {
+// J of each instance = sum of the partials of its data sets (fixed order)
+__global__ void k_sum_partials(const double* __restrict__ part, const int* __restrict__ kfirst, int ninst,
+                               double* __restrict__ J, int* __restrict__ flag) {
+    for (int inst = threadIdx.x; inst < ninst; inst += blockDim.x) {
         double s = 0.0;
-        for (int i = 0; i < np; ++i) s += part[i];
-        *J = s;
+        for (int i = kfirst[inst] * kResidBlocks; i < kfirst[inst + 1] * kResidBlocks; ++i) s += part[i];
+        J[inst] = s;
         if (!isfinite(s)) atomicOr(flag, 1);
     }
 }
@@ -524,6 +539,12 @@ static int check_launch(const char* what) {
     return PAT_OK;
 }
 
+// The dynamic shared-memory limit is a per-kernel attribute shared by every plan
+// of the process (and thread): it only ever grows, so that a plan of a smaller
+// grid never lowers it below what a larger plan launches with.
+static std::mutex g_smem_mu;
+static int g_smem_row = 0, g_smem_col = 0;
+
 int configure_kernels(pat_plan_s* p) {
     // keep rows per CTA even (pairs of real rows) and the shared memory in bounds
     int R = p->R;
@@ -531,13 +552,22 @@ int configure_kernels(pat_plan_s* p) {
     p->R = R;
     p->smem_row = size_t(p->ng + 2 * R * p->ng) * sizeof(float2);
     p->smem_col = size_t(p->ng + 4 * p->C * p->ng) * sizeof(float2);
-    const void* row_kernels[] = {(const void*)k_row_rho, (const void*)k_row_u, (const void*)k_row_adj_rho,
-                                 (const void*)k_row_adj_u, (const void*)k_row_adj_final1,
-                                 (const void*)k_row_adj_final2};
-    for (const void* f : row_kernels)
-        PAT_CUDA(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, int(p->smem_row)));
-    PAT_CUDA(cudaFuncSetAttribute((const void*)k_col, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  int(p->smem_col)));
+    {
+        std::lock_guard<std::mutex> lock(g_smem_mu);
+        if (int(p->smem_row) > g_smem_row) {
+            const void* row_kernels[] = {(const void*)k_row_rho, (const void*)k_row_u, (const void*)k_row_adj_rho,
+                                         (const void*)k_row_adj_u, (const void*)k_row_adj_final1,
+                                         (const void*)k_row_adj_final2};
+            for (const void* f : row_kernels)
+                PAT_CUDA(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, int(p->smem_row)));
+            g_smem_row = int(p->smem_row);
+        }
+        if (int(p->smem_col) > g_smem_col) {
+            PAT_CUDA(cudaFuncSetAttribute((const void*)k_col, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          int(p->smem_col)));
+            g_smem_col = int(p->smem_col);
+        }
+    }
     return select_variant(p, fixed_variants(p->ng) > 0 ? 0 : -1);
 }
 
@@ -564,7 +594,9 @@ static dim3 row_grid(const pat_plan_s* p) { return dim3((p->ng + p->R - 1) / p->
 int launch_medium(const Launch& L, const float* c_dom, float* cg) {
     const pat_plan_s* p = L.p;
     count_launch();
-    k_medium<<<(p->ng * p->ng + 255) / 256, 256, 0, L.st>>>(c_dom, cg, p->n, p->P, p->ng, float(p->g.c_bg));
+    const size_t tot = size_t(p->ninst) * p->ng * p->ng;
+    k_medium<<<unsigned(std::min<size_t>((tot + 255) / 256, 4096)), 256, 0, L.st>>>(c_dom, cg, p->n, p->P, p->ng,
+                                                                                 p->ninst, float(p->g.c_bg));
     return check_launch("k_medium");
 }
 
@@ -649,8 +681,10 @@ int launch_row_adj_final2(const Launch& L, const Ws& w, const float* p0, float* 
 int launch_reduce_cbar(const Launch& L, const Ws& w, float* grad_c) {
     const pat_plan_s* p = L.p;
     const int nn = p->n * p->n;
+    const size_t tot = size_t(p->ninst) * nn;
     count_launch();
-    k_reduce_cbar<<<(nn + 255) / 256, 256, 0, L.st>>>(w.cbar, grad_c, p->K, nn);
+    k_reduce_cbar<<<unsigned(std::min<size_t>((tot + 255) / 256, 4096)), 256, 0, L.st>>>(w.cbar, grad_c, p->t.kfirst,
+                                                                                       p->ninst, nn);
     return check_launch("k_reduce_cbar");
 }
 
@@ -659,11 +693,11 @@ int launch_residual(const Launch& L, const Ws& w, const float* ypred, const floa
     const pat_plan_s* p = L.p;
     PAT_CUDA(cudaMemsetAsync(w.flag, 0, sizeof(int), L.st));
     count_launch();
-    k_residual<<<kPartials, 256, 0, L.st>>>(ypred, ymeas, wts, resid, p->K, p->nt * p->m, w.part, w.flag);
+    k_residual<<<dim3(kResidBlocks, p->K), 256, 0, L.st>>>(ypred, ymeas, wts, resid, p->nt * p->m, w.part, w.flag);
     int rc = check_launch("k_residual");
     if (rc) return rc;
     count_launch();
-    k_sum_partials<<<1, 32, 0, L.st>>>(w.part, kPartials, J_out ? J_out : w.J, w.flag);
+    k_sum_partials<<<1, 128, 0, L.st>>>(w.part, p->t.kfirst, p->ninst, J_out ? J_out : w.J, w.flag);
     return check_launch("k_sum_partials");
 }
 

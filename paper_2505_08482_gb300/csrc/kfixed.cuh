@@ -315,7 +315,7 @@ __global__ void __launch_bounds__(RR * Fft2<N1, N2>::T) kf_row_rho(Geo g, float2
     const size_t row = size_t(k) * N + yy;
     float* rxr = rx + row * N;
     float* ryr = ry + row * N;
-    const float* cr = cg + size_t(yy) * N;
+    const float* cr = medium_of(g, cg, k) + size_t(yy) * N;
     // prologue: state, medium, PML (written two or more kernels earlier), twiddles
     float s0[N1], s1[N1], cc[N1], fa[N1];
     if (aact) {
@@ -441,7 +441,7 @@ __global__ void __launch_bounds__(RR * Fft2<N1, N2>::T) kf_row_adj_rho(Geo g, fl
     // pressure history (the segment recompute that writes it may be the preceding kernel)
     float s0[N1], s1[N1], cc[N1], hv[N1], fa[N1];
     if (aact) {
-        const float* cr = cg + size_t(yy) * N;
+        const float* cr = medium_of(g, cg, k) + size_t(yy) * N;
         static_for<0, N1>([&](auto I) {
             constexpr int n1 = decltype(I)::value;
             const int x = idx + N2 * n1;

@@ -4,8 +4,10 @@
 
 #include <cuda_runtime.h>
 
+#include <array>
 #include <cstddef>
 #include <string>
+#include <vector>
 
 #include "../../include/pat.h"
 #include "fft.cuh"
@@ -33,14 +35,16 @@ struct Tables {
     int* srow;         // [ng+1] CSR row pointer of sensor stencil entries
     int2* sent;        // [nent] (sensor m, column ix) per entry
     float4* sentw;     // [nent] (w_x0, w_x1, w_y, row) per entry
+    int* kinst;        // [K] instance of each data set
+    int* kfirst;       // [ninst+1] first data set of each instance
 };
 
 // Workspace regions (device pointers resolved from the caller's base).
 struct Ws {
     float* ux; float* uy; float* rx; float* ry;   // forward state [K][ng][ng] each (contiguous)
-    float* cg;                                    // c on the grid [ng][ng]
+    float* cg;                                    // c on the grid [ninst][ng][ng]
     float2* A; float2* B;                         // spectra [K][ng][hc]
-    double* J; double* part; int* flag;           // objective, partial sums, non-finite flag
+    double* J; double* part; int* flag;           // objective per instance, partial sums [K][32], flag
     // gradient only
     float* ckpt;                                  // [nseg-1][4][K][ng][ng]
     float* hist;                                  // [K][s_eff][ng][ng] pressure history
@@ -52,12 +56,14 @@ struct Ws {
 };
 
 constexpr int kPartials = 256;
+constexpr int kResidBlocks = 32;   // residual partial sums per data set
 
 }  // namespace pat
 
 struct pat_plan_s {
     pat_grid g;
     int n, P, ng, hc, hp, K, nt, m, s, s_eff, nseg;   // hp: spectrum row pitch (hc rounded up to 4)
+    int ninst;         // instances sharing the grid; K counts the data sets of all of them
     pat::FftDesc fft;
     const pat::FixedOps* fast;   // fixed-size passes for this grid side (nullptr: generic Stockham)
     int variant;       // -1 generic, else index of the fixed-size tile variant
@@ -74,6 +80,16 @@ struct pat_plan_s {
     // host bookkeeping: the workspace whose history holds the last segment
     const void* hist_valid_ws;
     int device;
+    // captured CUDA graphs of whole calls, keyed by call kind, buffers and variant
+    struct Graph {
+        int kind, variant;
+        std::array<const void*, 10> key;
+        size_t ws_bytes;
+        cudaGraphExec_t exec;
+        unsigned long long launches;
+    };
+    bool use_graphs;
+    std::vector<Graph> graphs;
 };
 
 namespace pat {
@@ -82,6 +98,8 @@ Ws resolve(const pat_plan_s* p, void* base, bool grad);
 
 // launch accounting / optional event timing of one kernel class (timing.cu)
 void count_launch();
+void add_launches(unsigned long long n);
+unsigned long long launches_so_far();
 void prof_begin(int cls, cudaStream_t st);
 void prof_end(int cls, cudaStream_t st);
 

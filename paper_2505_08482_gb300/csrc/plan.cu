@@ -105,11 +105,11 @@ static void layout(pat_plan_s* p) {
     const size_t spec = size_t(p->K) * p->ng * p->hp * sizeof(float2);
     size_t o = 0;
     p->o_state = o; o = align256(o + 4 * f);
-    p->o_cg = o; o = align256(o + size_t(p->ng) * p->ng * sizeof(float));
+    p->o_cg = o; o = align256(o + size_t(p->ninst) * p->ng * p->ng * sizeof(float));
     p->o_A = o; o = align256(o + spec);
     p->o_B = o; o = align256(o + spec);
-    p->o_J = o; o = align256(o + sizeof(double));
-    p->o_part = o; o = align256(o + kPartials * sizeof(double));
+    p->o_J = o; o = align256(o + size_t(p->ninst) * sizeof(double));
+    p->o_part = o; o = align256(o + size_t(p->K) * kResidBlocks * sizeof(double));
     p->o_flag = o; o = align256(o + 4 * sizeof(int));
     p->ws_fwd = o;
     p->o_ckpt = o; o = align256(o + size_t(std::max(p->nseg - 1, 0)) * 4 * f);
@@ -139,6 +139,13 @@ extern "C" int pat_pml_auto(int n, int min_pml) {
 
 extern "C" int pat_plan_ng(pat_plan plan) { return plan ? plan->ng : -1; }
 
+extern "C" int pat_plan_shape(pat_plan plan, int* ninst, int* K) {
+    if (!plan || !ninst || !K) { set_error("pat_plan_shape: null argument"); return PAT_EINVAL; }
+    *ninst = plan->ninst;
+    *K = plan->K;
+    return PAT_OK;
+}
+
 extern "C" int pat_plan_variants(pat_plan plan) { return plan ? fixed_variants(plan->ng) : -1; }
 
 extern "C" int pat_plan_set_variant(pat_plan plan, int variant) {
@@ -152,11 +159,34 @@ extern "C" int pat_plan_set_variant(pat_plan plan, int variant) {
 
 extern "C" int pat_plan_variant(pat_plan plan) { return plan ? plan->variant : -2; }
 
+extern "C" int pat_plan_set_graphs(pat_plan plan, int enable) {
+    if (!plan) { set_error("pat_plan_set_graphs: null plan"); return PAT_EINVAL; }
+    plan->use_graphs = enable != 0;
+    if (!plan->use_graphs) {
+        for (auto& g : plan->graphs) cudaGraphExecDestroy(g.exec);
+        plan->graphs.clear();
+    }
+    return PAT_OK;
+}
+
 extern "C" int pat_plan_create(pat_plan* out, const pat_grid* g, int m, const double* xy, int K,
                                int ckpt_every) {
-    if (!out || !g) { set_error("pat_plan_create: null argument"); return PAT_EINVAL; }
+    return pat_plan_create_batched(out, g, m, xy, 1, &K, ckpt_every);
+}
+
+extern "C" int pat_plan_create_batched(pat_plan* out, const pat_grid* g, int m, const double* xy, int ninst,
+                                       const int* h_K, int ckpt_every) {
+    if (!out || !g || !h_K) { set_error("pat_plan_create: null argument"); return PAT_EINVAL; }
     *out = nullptr;
-    if (g->n < 2 || g->pml < 0 || g->nt < 1 || K < 1 || m < 1 || !xy || ckpt_every < 1) {
+    if (ninst < 1 || ninst > 65536) { set_error("pat_plan_create: need 1 <= ninst <= 65536"); return PAT_EINVAL; }
+    long long Ktot = 0;
+    for (int i = 0; i < ninst; ++i) {
+        if (h_K[i] < 1) { set_error("pat_plan_create: instance %d has K < 1", i); return PAT_EINVAL; }
+        Ktot += h_K[i];
+    }
+    if (Ktot > 65535) { set_error("pat_plan_create: at most 65535 data sets per plan"); return PAT_EINVAL; }
+    const int K = int(Ktot);
+    if (g->n < 2 || g->pml < 0 || g->nt < 1 || m < 1 || !xy || ckpt_every < 1) {
         set_error("pat_plan_create: need n>=2, pml>=0, nt>=1, K>=1, m>=1, sensors, ckpt_every>=1");
         return PAT_EINVAL;
     }
@@ -178,12 +208,14 @@ extern "C" int pat_plan_create(pat_plan* out, const pat_grid* g, int m, const do
     p->hc = ng / 2 + 1;
     p->hp = (p->hc + 3) & ~3;
     p->K = K;
+    p->ninst = ninst;
     p->nt = g->nt;
     p->m = m;
     p->s = ckpt_every;
     p->s_eff = std::min(ckpt_every, g->nt);
     p->nseg = (g->nt + p->s_eff - 1) / p->s_eff;
     p->hist_valid_ws = nullptr;
+    p->use_graphs = false;
     cudaGetDevice(&p->device);
     radix_schedule(ng, &p->fft);
 
@@ -248,6 +280,12 @@ extern "C" int pat_plan_create(pat_plan* out, const pat_grid* g, int m, const do
     std::vector<int> srow(ng + 1, 0);
     for (const Ent& e : ents) srow[e.row + 1]++;
     for (int i = 0; i < ng; ++i) srow[i + 1] += srow[i];
+    std::vector<int> kinst(K), kfirst(ninst + 1, 0);
+    for (int i = 0, k = 0; i < ninst; ++i) {
+        kfirst[i] = k;
+        for (int j = 0; j < h_K[i]; ++j) kinst[k++] = i;
+    }
+    kfirst[ninst] = K;
     std::vector<int2> sent(p->nent);
     std::vector<float4> sentw(p->nent);
     for (int i = 0; i < p->nent; ++i) {
@@ -263,6 +301,7 @@ extern "C" int pat_plan_create(pat_plan* out, const pat_grid* g, int m, const do
     size_t o_ac = take(ng * sizeof(float)), o_as = take(ng * sizeof(float));
     size_t o_sr = take((ng + 1) * sizeof(int)), o_se = take(p->nent * sizeof(int2));
     size_t o_sw = take(p->nent * sizeof(float4));
+    size_t o_ki = take(K * sizeof(int)), o_kf = take((ninst + 1) * sizeof(int));
     cudaError_t e = cudaMalloc(&p->dev, o);
     if (e != cudaSuccess) {
         cuda_fail(e, "cudaMalloc(plan tables)");
@@ -279,6 +318,8 @@ extern "C" int pat_plan_create(pat_plan* out, const pat_grid* g, int m, const do
     p->t.srow = reinterpret_cast<int*>(d + o_sr);
     p->t.sent = reinterpret_cast<int2*>(d + o_se);
     p->t.sentw = reinterpret_cast<float4*>(d + o_sw);
+    p->t.kinst = reinterpret_cast<int*>(d + o_ki);
+    p->t.kfirst = reinterpret_cast<int*>(d + o_kf);
     struct Cp { void* dst; const void* src; size_t n; } cps[] = {
         {p->t.tw, tw.data(), ng * sizeof(float2)},
         {p->t.kappa_t, kap.data(), kap.size() * sizeof(float)},
@@ -289,6 +330,8 @@ extern "C" int pat_plan_create(pat_plan* out, const pat_grid* g, int m, const do
         {p->t.srow, srow.data(), (ng + 1) * sizeof(int)},
         {p->t.sent, sent.data(), p->nent * sizeof(int2)},
         {p->t.sentw, sentw.data(), p->nent * sizeof(float4)},
+        {p->t.kinst, kinst.data(), K * sizeof(int)},
+        {p->t.kfirst, kfirst.data(), (ninst + 1) * sizeof(int)},
     };
     for (const Cp& c : cps) {
         e = cudaMemcpy(c.dst, c.src, c.n, cudaMemcpyHostToDevice);
@@ -314,6 +357,7 @@ extern "C" int pat_plan_create(pat_plan* out, const pat_grid* g, int m, const do
 
 extern "C" void pat_plan_destroy(pat_plan p) {
     if (!p) return;
+    for (auto& g : p->graphs) cudaGraphExecDestroy(g.exec);
     if (p->dev) cudaFree(p->dev);
     delete p;
 }

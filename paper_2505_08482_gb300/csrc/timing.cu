@@ -2,6 +2,7 @@
 // recorded on the launching stream (used by the benchmark's roofline).
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <vector>
 
 #include "pat_internal.h"
@@ -18,10 +19,12 @@ struct Timing {
     std::vector<cudaEvent_t> t0, t1;
 };
 Timing g_t;
-unsigned long long g_launches = 0;
+std::atomic<unsigned long long> g_launches{0};   // batched solves may launch from several threads
 }  // namespace
 
 void count_launch() { ++g_launches; }
+void add_launches(unsigned long long n) { g_launches += n; }
+unsigned long long launches_so_far() { return g_launches.load(); }
 
 void prof_begin(int cls, cudaStream_t st) {
     ++g_launches;
@@ -42,7 +45,7 @@ void prof_end(int cls, cudaStream_t st) {
 
 using namespace pat;
 
-extern "C" unsigned long long pat_kernel_launches(void) { return g_launches; }
+extern "C" unsigned long long pat_kernel_launches(void) { return g_launches.load(); }
 
 extern "C" int pat_timing_enable(int cls, int max_launches, int every) {
     for (cudaEvent_t e : g_t.t0) cudaEventDestroy(e);

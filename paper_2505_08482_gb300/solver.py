@@ -58,11 +58,24 @@ class GridSpec:
 
 
 class Plan:
-    """A solver plan for K data sets on one grid (wraps pat_plan)."""
+    """A solver plan on one grid (wraps pat_plan).
 
-    def __init__(self, grid: GridSpec, sensors_xy, K: int, ckpt_every: int = 32, device=None):
+    ``K`` is the number of data sets of one reconstruction, or a sequence
+    with the number of data sets of each of several independent
+    reconstructions (instances) solved as one batch; then ``c`` and its
+    gradient are ``[ninst][n][n]`` and J is ``[ninst]``.
+    """
+
+    def __init__(self, grid: GridSpec, sensors_xy, K, ckpt_every: int = 32, device=None):
         self.grid = grid
-        self.K = int(K)
+        if np.ndim(K) == 0:
+            self.Ks = [int(K)]
+            self.batched = False
+        else:
+            self.Ks = [int(k) for k in K]
+            self.batched = True
+        self.ninst = len(self.Ks)
+        self.K = int(sum(self.Ks))
         self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
         xy = np.ascontiguousarray(np.asarray(sensors_xy, dtype=np.float64))
         if xy.ndim != 2 or xy.shape[1] != 2:
@@ -72,10 +85,11 @@ class Plan:
         self.n = grid.n
         g = B.PatGrid(grid.n, grid.pml, grid.dx, grid.dt, grid.nt, grid.c_ref, grid.rho0, grid.pml_alpha, grid.c_bg)
         h = ctypes.c_void_p()
+        ks = (ctypes.c_int * self.ninst)(*self.Ks)
         with torch.cuda.device(self.device):
-            B.check(B.lib().pat_plan_create(ctypes.byref(h), ctypes.byref(g), self.m,
-                                            xy.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), self.K,
-                                            int(ckpt_every)), "pat_plan_create")
+            B.check(B.lib().pat_plan_create_batched(ctypes.byref(h), ctypes.byref(g), self.m,
+                                                    xy.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), self.ninst,
+                                                    ks, int(ckpt_every)), "pat_plan_create_batched")
         self._h = h
         self.ckpt_every = int(ckpt_every)
         self._ws = {}
@@ -120,7 +134,8 @@ class Plan:
 
     def _shapes(self):
         n, K = self.n, self.K
-        return (n, n), (K, n, n), (K, self.nt, self.m)
+        sc = (self.ninst, n, n) if self.batched else (n, n)
+        return sc, (K, n, n), (K, self.nt, self.m)
 
     def forward(self, c, p0, y=None, keep_checkpoints=False, stream=None, ws=None):
         """Sensor traces y [K][nt][m] (pat_forward)."""
@@ -149,7 +164,7 @@ class Plan:
         if grad_c is None:
             grad_c = torch.empty(sc, dtype=torch.float32, device=self.device)
         if J is None:
-            J = torch.empty((), dtype=torch.float64, device=self.device)
+            J = torch.empty((self.ninst,) if self.batched else (), dtype=torch.float64, device=self.device)
         if y_pred is not None:
             _f32(y_pred, sy, "y_pred", self.device)
         if ws is None:
@@ -173,6 +188,20 @@ class Plan:
         B.check(B.lib().pat_vjp(self._h, _ptr(c), _ptr(p0), _ptr(ybar), _ptr(gp), _ptr(gc), _ptr(ws),
                                 self.workspace_bytes(B.PAT_WS_GRADIENT), _stream(stream)), "pat_vjp")
         return gp, gc
+
+    def set_graphs(self, enable: bool = True):
+        """Capture whole calls into CUDA graphs and replay them (pat_plan_set_graphs)."""
+        B.check(B.lib().pat_plan_set_graphs(self._h, int(bool(enable))), "pat_plan_set_graphs")
+
+    def autotune(self, stream=None):
+        """Time every kernel variant on this GPU and keep the fastest; returns ms/step per variant."""
+        nv = self.variants
+        ms = (ctypes.c_double * (max(nv, 0) + 1))()
+        ws = self.workspace(B.PAT_WS_FORWARD)
+        with torch.cuda.device(self.device):
+            B.check(B.lib().pat_plan_autotune(self._h, _ptr(ws), self.workspace_bytes(B.PAT_WS_FORWARD), ms,
+                                              _stream(stream)), "pat_plan_autotune")
+        return {v: ms[v + 1] for v in range(-1, max(nv, 0))}
 
     def nonfinite(self, stream=None) -> bool:
         """True if the last objective on the gradient workspace met NaN/Inf (synchronises)."""
@@ -207,6 +236,59 @@ class ReconConfig:
     alpha0: float = 0.1
     c1: float = 1e-4
     sigma_p0: float = 0.25
+    autotune: bool = False
+
+
+def _cfg_struct(cfg: ReconConfig, K: int, xy):
+    lv = (ctypes.c_int * len(cfg.levels))(*[int(v) for v in cfg.levels])
+    c_cfg = B.PatReconCfg(len(cfg.levels), lv, cfg.L, cfg.dt_data, cfg.nt_data, xy.shape[0],
+                          xy.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), K, cfg.cfl, cfg.c_lo, cfg.c_hi,
+                          cfg.p0_lo, cfg.c_bg, cfg.rho0, cfg.pml_alpha, cfg.min_pml, cfg.mem, cfg.iters,
+                          cfg.max_halvings, cfg.ckpt_every, cfg.rtol, cfg.alpha0, cfg.c1, cfg.sigma_p0,
+                          int(bool(cfg.autotune)))
+    return c_cfg, lv
+
+
+def _rows(rep, rows):
+    return [dict(level=r.level, it=r.iter, J=r.J, gnorm=r.gnorm, alpha=r.alpha, trials=r.trials, J_new=r.J_new,
+                 ms=r.ms) for r in rows[:rep.count]]
+
+
+def reconstruct_batched(cfg: ReconConfig, instances, stream=None, max_report=4096):
+    """Several reconstructions sharing cfg, solved together (pat_reconstruct_batched).
+
+    ``instances``: list of dicts with device tensors ``y_meas`` [K][nt][m],
+    ``w`` [K], ``c_init`` [N][N] and optional ``p0_init`` [K][N][N].  Returns a
+    list of (c, p0, report rows, status) and the total wall time in ms.
+    """
+    N = int(cfg.levels[-1])
+    xy = np.ascontiguousarray(np.asarray(cfg.sensors_xy, dtype=np.float64))
+    outs, structs, keep = [], [], []
+    for ins in instances:
+        ym, w = ins["y_meas"], ins["w"]
+        K = int(ym.shape[0])
+        dev = ym.device
+        _f32(ym, (K, cfg.nt_data, xy.shape[0]), "y_meas", dev)
+        _f32(w, (K,), "w", dev)
+        c = ins["c_init"].detach().clone().contiguous()
+        p0 = torch.zeros((K, N, N), dtype=torch.float32, device=dev) if ins.get("p0_init") is None else \
+            ins["p0_init"].detach().clone().contiguous()
+        _f32(c, (N, N), "c_init", dev)
+        _f32(p0, (K, N, N), "p0_init", dev)
+        rows = (B.PatIterReport * max_report)()
+        rep = B.PatReport(max_report, 0, rows, 0, 0.0)
+        keep.append((rows, rep))
+        structs.append(B.PatInstance(ym.data_ptr(), w.data_ptr(), c.data_ptr(), p0.data_ptr(), K,
+                                     ctypes.pointer(rep)))
+        outs.append((c, p0))
+    arr = (B.PatInstance * len(structs))(*structs)
+    c_cfg, lv = _cfg_struct(cfg, 0, xy)
+    dev = instances[0]["y_meas"].device
+    with torch.cuda.device(dev):
+        B.check(B.lib().pat_reconstruct_batched(ctypes.byref(c_cfg), len(structs), arr, _stream(stream)),
+                "pat_reconstruct_batched")
+    res = [(c, p0, _rows(rep, rows), int(rep.status)) for (c, p0), (rows, rep) in zip(outs, keep)]
+    return res, float(keep[0][1].total_ms)
 
 
 def reconstruct(cfg: ReconConfig, y_meas, w, c_init, p0_init=None, stream=None, max_report=4096):
@@ -226,16 +308,10 @@ def reconstruct(cfg: ReconConfig, y_meas, w, c_init, p0_init=None, stream=None, 
     xy = np.ascontiguousarray(np.asarray(cfg.sensors_xy, dtype=np.float64))
     _f32(y_meas, (K, cfg.nt_data, xy.shape[0]), "y_meas", dev)
     _f32(w, (K,), "w", dev)
-    lv = (ctypes.c_int * len(cfg.levels))(*[int(v) for v in cfg.levels])
-    c_cfg = B.PatReconCfg(len(cfg.levels), lv, cfg.L, cfg.dt_data, cfg.nt_data, xy.shape[0],
-                          xy.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), K, cfg.cfl, cfg.c_lo, cfg.c_hi,
-                          cfg.p0_lo, cfg.c_bg, cfg.rho0, cfg.pml_alpha, cfg.min_pml, cfg.mem, cfg.iters,
-                          cfg.max_halvings, cfg.ckpt_every, cfg.rtol, cfg.alpha0, cfg.c1, cfg.sigma_p0)
+    c_cfg, lv = _cfg_struct(cfg, K, xy)
     rows = (B.PatIterReport * max_report)()
     rep = B.PatReport(max_report, 0, rows, 0, 0.0)
     with torch.cuda.device(dev):
         B.check(B.lib().pat_reconstruct(ctypes.byref(c_cfg), _ptr(y_meas), _ptr(w), _ptr(c), _ptr(p0),
                                         ctypes.byref(rep), _stream(stream)), "pat_reconstruct")
-    out = [dict(level=r.level, it=r.iter, J=r.J, gnorm=r.gnorm, alpha=r.alpha, trials=r.trials, J_new=r.J_new,
-                ms=r.ms) for r in rows[:rep.count]]
-    return c, p0, out, int(rep.status), float(rep.total_ms)
+    return c, p0, _rows(rep, rows), int(rep.status), float(rep.total_ms)
