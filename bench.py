@@ -83,6 +83,12 @@ def parse():
     ap.add_argument("--batch-instances", type=int, default=64)
     ap.add_argument("--batch-iters", type=int, default=2)
     ap.add_argument("--batch-plain", type=int, default=64, help="instances also solved one by one")
+    ap.add_argument("--warmstart", action="store_true",
+                    help="learned warm start: train the U-Net on solver-generated pairs, compare with the plain start")
+    ap.add_argument("--ws-train", type=int, default=20000)
+    ap.add_argument("--ws-test", type=int, default=512)
+    ap.add_argument("--ws-epochs", type=int, default=12)
+    ap.add_argument("--ws-iters", type=int, default=20)
     return ap.parse_args()
 
 
@@ -507,6 +513,74 @@ def run_batch(args):
     print(json.dumps(line), flush=True)
 
 
+def run_warmstart(args):
+    """Learned warm start (128x128, K=4): iterations and time to E_c <= 2 % with and without it."""
+    import numpy as np
+    import torch
+
+    import paper_2505_08482_gb300 as pkg
+    from paper_2505_08482_gb300 import _binding as B
+    from paper_2505_08482_gb300.solver import ReconConfig, reconstruct_batched
+    from paper_2505_08482_gb300.warmstart import (PairGenerator, UNet, init_params, iterations_to, predict_c,
+                                                  relative_error, train)
+    pkg.build()
+    torch.cuda.set_device(0)
+    n, K = 128, 4
+    gen = PairGenerator(n=n, K=K, M=256, nt=600, batch=64)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    X, T, _ = gen.make(list(range(args.ws_train)))
+    torch.cuda.synchronize()
+    t_gen = time.perf_counter() - t0
+    net = UNet(4, 32, K, n, n, max_batch=32)
+    net.set_params(init_params(4, 32, K, seed=1))
+    t0 = time.perf_counter()
+    launches0 = B.lib().pat_kernel_launches()
+    hist = train(net, X, T, epochs=args.ws_epochs, batch=32, lr=1e-3)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    train_launches = int(B.lib().pat_kernel_launches() - launches0)
+    del X, T
+    Xh, Th, raw = gen.make(list(range(10 ** 6, 10 ** 6 + args.ws_test)), keep_data=True)
+    c_true = torch.stack([r["c_true"] for r in raw])
+    c_warm = predict_c(net, Xh)
+    c_plain = torch.stack([torch.full_like(ct, 0.5 * float(ct.min() + ct.max())) for ct in c_true])
+    e_warm0 = relative_error(c_warm, c_true).cpu().numpy()
+    e_plain0 = relative_error(c_plain, c_true).cpu().numpy()
+    cfg = ReconConfig(levels=(64, 128), L=n * 1e-4, dt_data=gen.gs.dt, nt_data=gen.nt, sensors_xy=gen.sensors, K=K,
+                      iters=args.ws_iters, mem=20, ckpt_every=32, rtol=0.0)
+    arms = {}
+    for name, cinit in (("plain", c_plain), ("warm", c_warm)):
+        its, mss, fin = [], [], []
+        t0 = time.perf_counter()
+        for b0 in range(0, len(raw), 64):
+            insts = [dict(y_meas=r["y_meas"].contiguous(), w=r["w"].contiguous(), c_init=cinit[b0 + j].contiguous(),
+                          c_true=r["c_true"].contiguous(), ec_target=2.0) for j, r in enumerate(raw[b0:b0 + 64])]
+            res, _ = reconstruct_batched(cfg, insts)
+            for c_rec, _, rows, _ in res:
+                i_, m_ = iterations_to(rows, 2.0, 2)
+                its.append(i_)
+                mss.append(m_)
+                fin.append([r["Ec"] for r in rows if r["level"] == 1][-1] if rows else None)
+        wall = time.perf_counter() - t0
+        reached = [i for i in its if i is not None]
+        arms[name] = {"reached_2pct": len(reached) / len(its),
+                      "iterations_median": float(np.median(reached)) if reached else None,
+                      "ms_median": float(np.median([m for m in mss if m is not None])) if reached else None,
+                      "final_Ec_median": float(np.median([f for f in fin if f is not None])),
+                      "wall_s": wall}
+    line = {"metric": "learned warm start: iterations / time to E_c <= 2 %", "unit": "iterations",
+            "value": arms["warm"]["iterations_median"], "higher_is_better": False, "n_gpus": 1, "dtype": "bf16+f32",
+            "data": "synthetic",
+            "config": {"workload": f"U-Net 4 levels x 32, {args.ws_train} solver-generated pairs (128x128, K=4, "
+                                   f"M=256, Nt=600), {args.ws_test} held-out seeds, levels 64->128, "
+                                   f"<= {args.ws_iters} L-BFGS iterations per level"},
+            "pair_generation_s": t_gen, "training_s": t_train, "train_loss": hist, "training_launches": train_launches,
+            "initial_Ec_median": {"plain": float(np.median(e_plain0)), "warm": float(np.median(e_warm0))},
+            "arms": arms}
+    print(json.dumps(line), flush=True)
+
+
 def ctypes_read(L):
     import ctypes
     tot = ctypes.c_double(0.0)
@@ -527,6 +601,9 @@ def main():
         return
     if args.batch:
         run_batch(args)
+        return
+    if args.warmstart:
+        run_warmstart(args)
         return
     if world > 1:
         import torch

@@ -248,6 +248,8 @@ typedef struct {
     int trials;     /* objective evaluations in the line search */
     double J_new;   /* objective after the step */
     double ms;      /* wall time of the iteration */
+    double Ec;      /* E_c (%, Eq. RelativeError) after the step against the instance's
+                       true c resampled to the level, or -1 without a true c */
 } pat_iter_report;
 
 typedef struct {
@@ -306,6 +308,8 @@ typedef struct {
     float* d_p0_io;
     int K;
     pat_report* report;
+    const float* d_c_true;   /* optional [N][N]: report E_c per iteration */
+    double ec_target;        /* > 0 with d_c_true: stop once E_c <= ec_target on the finest level */
 } pat_instance;
 
 /* Several independent reconstructions that share cfg (levels, domain,
@@ -317,6 +321,41 @@ typedef struct {
  * keeps its point).  Results are those of pat_reconstruct on each instance
  * alone.  Synchronises the stream once per evaluation round. */
 int pat_reconstruct_batched(const pat_recon_cfg* cfg, int ninst, const pat_instance* inst, void* stream);
+
+/* ---- learned warm start (spec extension; the paper has no network) ----
+ * A U-Net mapping K back-projected images (adjoint solves at a constant
+ * speed of sound, i.e. pat_vjp with c = c0) to an initial speed-of-sound map
+ * for pat_reconstruct; the iterative solve stays the judge of the result.
+ * Encoder level l (0..levels-1): two 3x3 convolutions + ReLU with base*2^l
+ * channels and 2x2 max pooling between levels; decoder: nearest 2x
+ * upsampling, concatenation [upsampled, encoder] and two 3x3 convolutions +
+ * ReLU; a final 1x1 convolution to one channel.  BF16 activations and
+ * weights on the tensor cores, FP32 accumulation, FP32 master parameters
+ * and Adam.  The model owns its buffers (allocated at creation for
+ * max_batch images). */
+typedef struct pat_unet_s* pat_unet;
+int pat_unet_create(pat_unet* out, int levels, int base, int in_ch, int H, int W, int max_batch);
+void pat_unet_destroy(pat_unet net);
+/* Number of FP32 parameters.  Layout: for every convolution in forward order
+ * (encoder a/b per level, decoder a/b per level from the deepest, final),
+ * weights [cout][k*k][cin] then bias [cout]; cin of the first convolution is
+ * in_ch rounded up to 8 (weights of the padding channels must be 0). */
+size_t pat_unet_param_count(pat_unet net);
+/* h_desc: host int[6 * n_convs] (may be NULL): cin, cout, k, weight offset,
+ * bias offset, spatial side of each convolution. */
+int pat_unet_param_layout(pat_unet net, int* n_convs, int* h_desc);
+/* Device FP32 parameters in / out (set also resets the Adam moments). */
+int pat_unet_set_params(pat_unet net, const float* d_params, void* stream);
+int pat_unet_get_params(pat_unet net, float* d_params, void* stream);
+/* d_in: device [B][in_ch][H][W] FP32; d_out: device [B][H][W] FP32. */
+int pat_unet_forward(pat_unet net, const float* d_in, int B, float* d_out, void* stream);
+/* MSE loss mean((out - target)^2) (device double, may be NULL) and the FP32
+ * parameter gradients (device, parameter layout; may be NULL). */
+int pat_unet_grads(pat_unet net, const float* d_in, const float* d_target, int B, float* d_grad, double* d_loss,
+                   void* stream);
+/* One Adam step (beta 0.9 / 0.999, eps 1e-8) with learning rate lr. */
+int pat_unet_train_step(pat_unet net, const float* d_in, const float* d_target, int B, float lr, double* d_loss,
+                        void* stream);
 
 /* Message describing the last error on the calling thread. */
 const char* pat_last_error(void);

@@ -54,7 +54,7 @@ class PatInstance(ctypes.Structure):
 
 class PatIterReport(ctypes.Structure):
     _fields_ = [("level", c_int), ("iter", c_int), ("J", c_double), ("gnorm", c_double), ("alpha", c_double),
-                ("trials", c_int), ("J_new", c_double), ("ms", c_double)]
+                ("trials", c_int), ("J_new", c_double), ("ms", c_double), ("Ec", c_double)]
 
 
 class PatReport(ctypes.Structure):
@@ -63,7 +63,8 @@ class PatReport(ctypes.Structure):
 
 
 PatInstance._fields_ = [("d_y_meas", c_void_p), ("d_w", c_void_p), ("d_c_io", c_void_p), ("d_p0_io", c_void_p),
-                        ("K", c_int), ("report", POINTER(PatReport))]
+                        ("K", c_int), ("report", POINTER(PatReport)), ("d_c_true", c_void_p),
+                        ("ec_target", c_double)]
 
 # name -> (restype, argtypes)
 SIGNATURES = {
@@ -92,6 +93,15 @@ SIGNATURES = {
     "pat_kernel_launches": (ctypes.c_ulonglong, []),
     "pat_timing_enable": (c_int, [c_int, c_int, c_int]),
     "pat_timing_read": (c_int, [POINTER(c_double), POINTER(ctypes.c_longlong)]),
+    "pat_unet_create": (c_int, [POINTER(c_void_p), c_int, c_int, c_int, c_int, c_int, c_int]),
+    "pat_unet_destroy": (None, [c_void_p]),
+    "pat_unet_param_count": (c_size_t, [c_void_p]),
+    "pat_unet_param_layout": (c_int, [c_void_p, POINTER(c_int), POINTER(c_int)]),
+    "pat_unet_set_params": (c_int, [c_void_p, c_void_p, c_void_p]),
+    "pat_unet_get_params": (c_int, [c_void_p, c_void_p, c_void_p]),
+    "pat_unet_forward": (c_int, [c_void_p, c_void_p, c_int, c_void_p, c_void_p]),
+    "pat_unet_grads": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_void_p, c_void_p, c_void_p]),
+    "pat_unet_train_step": (c_int, [c_void_p, c_void_p, c_void_p, c_int, ctypes.c_float, c_void_p, c_void_p]),
     "pat_last_error": (c_char_p, []),
 }
 

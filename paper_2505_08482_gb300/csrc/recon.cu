@@ -44,12 +44,13 @@ using Clock = std::chrono::steady_clock;
 double ms_since(Clock::time_point t) { return std::chrono::duration<double, std::milli>(Clock::now() - t).count(); }
 
 // scalar slots per instance in the device scalar array
-enum { S_GD, S_DEC, S_GG, S_SY, S_SS, S_YY, S_MAX, S_BETA, S_H0, S_COUNT };
+enum { S_GD, S_DEC, S_GG, S_SY, S_SS, S_YY, S_MAX, S_BETA, S_H0, S_EC, S_CT, S_COUNT };
 
 struct Inst {
     int K;
     size_t V, n0;               // vector length, length of the p0 block
     float *x, *z, *g, *d, *xt, *zt, *gt, *q, *psi;
+    float* ct = nullptr;        // true c resampled to the level (E_c tracking), or null
     std::vector<float*> S, Y;   // ring of curvature pairs
     double* lam;                // [mem] device
     double* rho;                // [mem] device
@@ -248,7 +249,13 @@ int Batch::level(int li, const float* const* xprev, int nprev) {
         RC(vresample(st, xprev[i], s.xt, s.K + 1, nprev, N));
         RC(vblockscale(st, s.zt, s.xt, s.V, s.n0, float(sp), float(sc_c), 1));
         RC(vproject(st, s.z, s.x, s.zt, s.zt, 0.f, s.V, s.n0, box));
+        if (ins[i].d_c_true) {
+            RC(alloc(&s.ct, nn));
+            RC(vresample(st, ins[i].d_c_true, s.ct, 1, cfg.levels[cfg.nlevels - 1], N));
+            RC(vdot(st, s.ct, s.ct, nn, sc(i, S_CT), part));
+        }
     }
+    const bool finest = li == cfg.nlevels - 1;
     RC(evaluate(true, false));
     for (int i = 0; i < ni; ++i) I[i].J = hJ[i];
     for (int it = 0; it < cfg.iters; ++it) {
@@ -348,8 +355,8 @@ int Batch::level(int li, const float* const* xprev, int nprev) {
             pat_report* rep = ins[i].report;
             if (rep) {
                 if (rep->count < rep->capacity && rep->iters)
-                    rep->iters[rep->count++] =
-                        pat_iter_report{li, it, s.J, std::sqrt(hs(i, S_GG)), 0.0, s.trials, s.J, ms_since(s.t_iter)};
+                    rep->iters[rep->count++] = pat_iter_report{
+                        li, it, s.J, std::sqrt(hs(i, S_GG)), 0.0, s.trials, s.J, ms_since(s.t_iter), -1.0};
                 rep->status = PAT_ELINESEARCH;
             }
             s.active = false;
@@ -373,6 +380,10 @@ int Batch::level(int li, const float* const* xprev, int nprev) {
             RC(vdot(st, s.S[slot], s.Y[slot], s.V, sc(i, S_SY), part));
             RC(vdot(st, s.S[slot], s.S[slot], s.V, sc(i, S_SS), part));
             RC(vdot(st, s.Y[slot], s.Y[slot], s.V, sc(i, S_YY), part));
+            if (s.ct) {   // E_c of the accepted point: || c - c_true ||^2 via the scratch vector q
+                RC(vaxpby(st, s.q, 1.f, s.xt + s.n0, -1.f, s.ct, nn));
+                RC(vdot(st, s.q, s.q, nn, sc(i, S_EC), part));
+            }
         }
         RC(sync_scalars());
         for (int i : act) {
@@ -395,16 +406,18 @@ int Batch::level(int li, const float* const* xprev, int nprev) {
                 }
             }
             const double Jn = hJ[i];
+            const double ec = s.ct ? 100.0 * std::sqrt(hs(i, S_EC) / hs(i, S_CT)) : -1.0;
             pat_report* rep = ins[i].report;
             if (rep && rep->count < rep->capacity && rep->iters)
-                rep->iters[rep->count++] =
-                    pat_iter_report{li, it, s.J, std::sqrt(hs(i, S_GG)), s.alpha, s.trials, Jn, ms_since(s.t_iter)};
+                rep->iters[rep->count++] = pat_iter_report{li,      it, s.J, std::sqrt(hs(i, S_GG)), s.alpha,
+                                                           s.trials, Jn, ms_since(s.t_iter), ec};
             const double rel = s.J > 0 ? (s.J - Jn) / s.J : 0.0;
             std::swap(s.z, s.zt);
             std::swap(s.x, s.xt);
             std::swap(s.g, s.gt);
             s.J = Jn;
             if (rel < cfg.rtol) s.active = false;
+            if (finest && s.ct && ins[i].ec_target > 0 && ec <= ins[i].ec_target) s.active = false;
         }
     }
     return PAT_OK;
@@ -499,6 +512,6 @@ extern "C" int pat_reconstruct(const pat_recon_cfg* cfg, const float* y_meas, co
                                float* p0_io, pat_report* rep, void* stream) {
     if (!cfg || !y_meas || !w || !c_io || !p0_io) { set_error("pat_reconstruct: null argument"); return PAT_EINVAL; }
     if (cfg->K < 1) { set_error("pat_reconstruct: K < 1"); return PAT_EINVAL; }
-    pat_instance one{y_meas, w, c_io, p0_io, cfg->K, rep};
+    pat_instance one{y_meas, w, c_io, p0_io, cfg->K, rep, nullptr, 0.0};
     return pat_reconstruct_batched(cfg, 1, &one, stream);
 }

@@ -251,15 +251,17 @@ def _cfg_struct(cfg: ReconConfig, K: int, xy):
 
 def _rows(rep, rows):
     return [dict(level=r.level, it=r.iter, J=r.J, gnorm=r.gnorm, alpha=r.alpha, trials=r.trials, J_new=r.J_new,
-                 ms=r.ms) for r in rows[:rep.count]]
+                 ms=r.ms, Ec=r.Ec) for r in rows[:rep.count]]
 
 
 def reconstruct_batched(cfg: ReconConfig, instances, stream=None, max_report=4096):
     """Several reconstructions sharing cfg, solved together (pat_reconstruct_batched).
 
     ``instances``: list of dicts with device tensors ``y_meas`` [K][nt][m],
-    ``w`` [K], ``c_init`` [N][N] and optional ``p0_init`` [K][N][N].  Returns a
-    list of (c, p0, report rows, status) and the total wall time in ms.
+    ``w`` [K], ``c_init`` [N][N] and optional ``p0_init`` [K][N][N], ``c_true``
+    [N][N] (E_c per iteration) and ``ec_target`` (stop once E_c is reached on
+    the finest level).  Returns a list of (c, p0, report rows, status) and the
+    total wall time in ms.
     """
     N = int(cfg.levels[-1])
     xy = np.ascontiguousarray(np.asarray(cfg.sensors_xy, dtype=np.float64))
@@ -278,8 +280,12 @@ def reconstruct_batched(cfg: ReconConfig, instances, stream=None, max_report=409
         rows = (B.PatIterReport * max_report)()
         rep = B.PatReport(max_report, 0, rows, 0, 0.0)
         keep.append((rows, rep))
+        ct = ins.get("c_true")
+        if ct is not None:
+            _f32(ct, (N, N), "c_true", dev)
         structs.append(B.PatInstance(ym.data_ptr(), w.data_ptr(), c.data_ptr(), p0.data_ptr(), K,
-                                     ctypes.pointer(rep)))
+                                     ctypes.pointer(rep), ct.data_ptr() if ct is not None else None,
+                                     float(ins.get("ec_target", 0.0))))
         outs.append((c, p0))
     arr = (B.PatInstance * len(structs))(*structs)
     c_cfg, lv = _cfg_struct(cfg, 0, xy)

@@ -13,7 +13,9 @@ phantom of Sec. 4.1.1), 1 % additive Gaussian noise relative to the
 peak-to-peak amplitude of each data set (Sec. 4.1.1), and point sensors.
 """
 from .phantoms import (ellipse_phantom, blob_p0, vessel_p0, circle_sensors,
-                       add_noise, noise_weights, workload, Workload, rng_for)
+                       add_noise, noise_weights, workload, Workload, rng_for,
+                       add_noise_torch, warmstart_sample)
 
 __all__ = ["ellipse_phantom", "blob_p0", "vessel_p0", "circle_sensors",
-           "add_noise", "noise_weights", "workload", "Workload", "rng_for"]
+           "add_noise", "noise_weights", "workload", "Workload", "rng_for",
+           "add_noise_torch", "warmstart_sample"]

@@ -201,3 +201,24 @@ def workload(name: str, seed: int = 0) -> Workload:
         raise ValueError(f"unknown workload {name!r}")
     sensors = circle_sensors(n, M, dx)
     return Workload(n=n, dx=dx, nt=nt, c_true=c, p0_true=p0, sensors=sensors, seed=seed)
+
+
+def add_noise_torch(y, gen, rel: float = 0.01):
+    """Torch (GPU) version of add_noise for large training sets: y [K][Nt][M] per data set.
+
+    Returns (noisy y, weights 1/(rel p2p(noisy))^2) with a seeded torch.Generator on y's device.
+    """
+    import torch
+    p2p = (y.amax(dim=(1, 2)) - y.amin(dim=(1, 2))).clamp_min(1e-30)
+    noise = torch.randn(y.shape, generator=gen, device=y.device, dtype=y.dtype)
+    yn = y + (rel * p2p)[:, None, None] * noise
+    p2pn = (yn.amax(dim=(1, 2)) - yn.amin(dim=(1, 2))).clamp_min(1e-30)
+    return yn, 1.0 / (rel * p2pn) ** 2
+
+
+def warmstart_sample(n: int, K: int, seed: int):
+    """c with 2-8 random inclusions in [1400, 1650] m/s and K vessel-like p0 sets (learned warm start data)."""
+    rng = rng_for(seed)
+    c = ellipse_phantom(n, int(rng.integers(2, 9)), rng)
+    p0 = np.stack([vessel_p0(n, rng) for _ in range(K)])
+    return c, p0
