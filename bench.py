@@ -60,12 +60,15 @@ def bytes_per_cell(cls: int, ng: int, n: int, ckpt_hist: bool = True) -> float:
     return table[cls]
 
 
+KERNEL_FILES = ("fft.cuh", "fft2l.cuh", "geo.cuh", "kfixed.cuh", "kfixed_300.cu", "kernels.cu")
+
+
 def kernel_source_hash() -> str:
+    """Hash of the sources of the solver kernels (the profiles are valid while it is unchanged)."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2505_08482_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
-        if f.endswith((".cu", ".cuh", ".h")):
-            h.update(open(os.path.join(csrc, f), "rb").read())
+    for f in KERNEL_FILES:
+        h.update(open(os.path.join(csrc, f), "rb").read())
     return h.hexdigest()[:16]
 
 
@@ -76,6 +79,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--ckpt", type=int, default=WL["ckpt_every"])
+    ap.add_argument("--nt", type=int, default=WL["nt"], help="time samples (fewer only for profiling captures)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-steps", type=int, default=0, help="oracle sample length (0 = auto)")
     ap.add_argument("--batch", action="store_true",
@@ -247,13 +251,14 @@ def run_ours(args, rank, world, local_rank):
     dev = torch.device("cuda", local_rank)
     L = B.lib()
     w, c_init = inputs(rank)
-    n, K, M, nt = WL["n"], WL["K"], WL["M"], WL["nt"]
+    n, K, M, nt = WL["n"], WL["K"], WL["M"], args.nt
     P = pml_auto(n)
     dt = WL["cfl"] * WL["dx"] / WL["c_hi"]
     gs = GridSpec(n=n, pml=P, dx=WL["dx"], dt=dt, nt=nt, c_ref=WL["c_hi"], pml_alpha=WL["pml_alpha"],
                   c_bg=WL["c_bg"])
     ng = gs.ng
     plan = Plan(gs, w.sensors, K, ckpt_every=args.ckpt, device=dev)
+    tuned = plan.autotune()           # the library's autotuner picks the tile variant on this GPU
     f32 = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float32, device=dev)
     c_true, p0_true = f32(w.c_true), f32(w.p0_true)
     y_clean = plan.forward(c_true, p0_true).cpu().numpy()
@@ -389,7 +394,8 @@ def run_ours(args, rank, world, local_rank):
             "forward_gcell_steps_per_s": gcell * world, "forward_ms": fwd_s * 1000.0,
             "grad_gcell_steps_per_s": value * ng * ng * K * (nt - 1) / 1e9,
             "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-            "gpu_launches": launches, "roofline": roof, "clocks": clocks, "kernel_source_hash": src_hash}
+            "gpu_launches": launches, "roofline": roof, "clocks": clocks, "kernel_source_hash": src_hash,
+            "autotune_ms_per_step": {str(v): round(t, 4) for v, t in tuned.items()}, "variant": plan.variant}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         nt_s = args.cpu_sample_steps or 300
         ts = oracle_sample(0, nt_s)

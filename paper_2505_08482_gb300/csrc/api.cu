@@ -52,21 +52,42 @@ int pat::forward_sweep(pat_plan_s* p, const float* c, const float* p0, float* y,
     RC(launch_medium(L, c, w.cg));
     PAT_CUDA(cudaMemsetAsync(y, 0, size_t(p->K) * p->nt * p->m * sizeof(float), st));
     const int last0 = (p->nseg - 1) * p->s_eff;
-    RC(launch_row_rho(L, w, 1, p0, y, 0, (keep && last0 == 0) ? w.hist : nullptr, 0));
+    float* hlast = keep ? hist_of(p, w, p->nseg - 1) : nullptr;
+    RC(launch_row_rho(L, w, 1, p0, y, 0, (keep && last0 == 0) ? hlast : nullptr, 0));
     for (int n = 0; n + 1 < p->nt; ++n) {
         if (keep && n > 0 && n % p->s_eff == 0) {
             PAT_CUDA(cudaMemcpyAsync(w.ckpt + size_t(n / p->s_eff - 1) * 4 * p->K * p->ng * p->ng, w.ux,
                                      state_bytes(p), cudaMemcpyDeviceToDevice, st));
         }
         const bool h = keep && (n + 1) >= last0;
-        RC(step(L, w, n, y, h ? w.hist : nullptr, n + 1 - last0));
+        RC(step(L, w, n, y, h ? hlast : nullptr, n + 1 - last0));
     }
     return PAT_OK;
 }
 
 namespace {
 
-// reverse sweep with the weighted residual (or adjoint source) r [K][nt][m]
+// recompute segment j's pressure history into its buffer (on stream st)
+int recompute(pat_plan_s* p, const float* p0, const Ws& w, int j, cudaStream_t st) {
+    Launch L{p, st};
+    const size_t f = size_t(p->K) * p->ng * p->ng;
+    const int n0 = j * p->s_eff;
+    const int n1 = std::min(n0 + p->s_eff, p->nt) - 1;
+    float* h = hist_of(p, w, j);
+    if (j == 0) {
+        RC(launch_row_rho(L, w, 1, p0, nullptr, 0, h, 0));
+    } else {
+        PAT_CUDA(cudaMemcpyAsync(w.ux, w.ckpt + size_t(j - 1) * 4 * f, state_bytes(p), cudaMemcpyDeviceToDevice,
+                                 st));
+        RC(launch_row_rho(L, w, 2, nullptr, nullptr, 0, h, 0));
+    }
+    for (int n = n0; n < n1; ++n) RC(step(L, w, n, nullptr, h, n + 1 - n0));
+    return PAT_OK;
+}
+
+// reverse sweep with the weighted residual (or adjoint source) r [K][nt][m].
+// The recompute of segment j-1 runs on the plan's second stream while the adjoint
+// steps of segment j run on st; the two pressure-history buffers alternate.
 int reverse_sweep(pat_plan_s* p, const float* p0, const float* r, float* grad_p0, float* grad_c, const Ws& w,
                   bool hist_last_valid, cudaStream_t st) {
     Launch L{p, st};
@@ -75,27 +96,38 @@ int reverse_sweep(pat_plan_s* p, const float* p0, const float* r, float* grad_p0
     PAT_CUDA(cudaMemsetAsync(w.cbar, 0, size_t(p->K) * p->n * p->n * sizeof(float), st));
     const float sg = float(p->g.dt * p->g.rho0 / (double(p->ng) * p->ng));   // dt rho0 G t
     const float sd = float(p->g.dt / p->g.rho0 / (double(p->ng) * p->ng));   // dt/rho0 D t'
+    cudaStream_t R = p->side;
+    const int last = p->nseg - 1;
+    // the side stream starts after everything issued so far on st (forward sweep, residual)
+    PAT_CUDA(cudaEventRecord(p->ev_start, st));
+    PAT_CUDA(cudaStreamWaitEvent(R, p->ev_start, 0));
+    if (!hist_last_valid) {
+        RC(recompute(p, p0, w, last, R));
+        PAT_CUDA(cudaEventRecord(p->ev_rec[last & 1], R));
+    }
+    if (last >= 1) {
+        RC(recompute(p, p0, w, last - 1, R));
+        PAT_CUDA(cudaEventRecord(p->ev_rec[(last - 1) & 1], R));
+    }
     bool have_q = false;
-    for (int j = p->nseg - 1; j >= 0; --j) {
+    for (int j = last; j >= 0; --j) {
         const int n0 = j * p->s_eff;
         const int n1 = std::min(n0 + p->s_eff, p->nt) - 1;
-        if (!(j == p->nseg - 1 && hist_last_valid)) {
-            // recompute the segment's pressure history
-            if (j == 0) {
-                RC(launch_row_rho(L, w, 1, p0, nullptr, 0, w.hist, 0));
-            } else {
-                PAT_CUDA(cudaMemcpyAsync(w.ux, w.ckpt + size_t(j - 1) * 4 * f, state_bytes(p),
-                                         cudaMemcpyDeviceToDevice, st));
-                RC(launch_row_rho(L, w, 2, nullptr, nullptr, 0, w.hist, 0));
-            }
-            for (int n = n0; n < n1; ++n) RC(step(L, w, n, nullptr, w.hist, n + 1 - n0));
-        }
+        if (j < last || !hist_last_valid) PAT_CUDA(cudaStreamWaitEvent(st, p->ev_rec[j & 1], 0));
+        const float* h = hist_of(p, w, j);
         for (int n = n1; n >= std::max(n0, 1); --n) {
-            RC(launch_row_adj_rho(L, w, have_q ? 0 : 1, r, n, w.hist, n - n0));
+            RC(launch_row_adj_rho(L, w, have_q ? 0 : 1, r, n, h, n - n0));
             RC(launch_col(L, w.A2, w.B2, 1, 0, sg));
             RC(launch_row_adj_u(L, w));
             RC(launch_col(L, w.A2, w.B2, 2, 1, sd));
             have_q = true;
+        }
+        // segment j - 2 reuses this segment's buffer once its adjoint steps are done
+        if (j - 2 >= 0) {
+            PAT_CUDA(cudaEventRecord(p->ev_adj[j & 1], st));
+            PAT_CUDA(cudaStreamWaitEvent(R, p->ev_adj[j & 1], 0));
+            RC(recompute(p, p0, w, j - 2, R));
+            PAT_CUDA(cudaEventRecord(p->ev_rec[(j - 2) & 1], R));
         }
     }
     RC(launch_row_adj_final1(L, w, have_q ? 0 : 1, r, grad_p0));

@@ -84,30 +84,29 @@ __device__ __forceinline__ void col_mults(const Geo& g, int kx, int ky, int op, 
 
 // ---------------------------------------------------------------------------
 // column pass; mode 0: A -> (MX A, MY A) into (A, B); 1: (A, B) -> (MX A, MY B); 2: MX A + MY B -> A.
-// All global loads (the columns and the multiplier tables) are issued before the first barrier.
+// The two fields (or the two outputs) of a column are handled by separate threads (f = 0, 1).
+// Tables and twiddles are loaded before the dependency wait, the columns after it.
 template <int N1, int N2, int CC>
-__global__ void __launch_bounds__(CC * Fft2<N1, N2>::T) kf_col(Geo g, float2* __restrict__ A,
-                                                              float2* __restrict__ B, int mode, int op,
-                                                              float scale) {
+__global__ void __launch_bounds__(2 * CC * Fft2<N1, N2>::T) kf_col(Geo g, float2* __restrict__ A,
+                                                                  float2* __restrict__ B, int mode, int op,
+                                                                  float scale) {
     using F = Fft2<N1, N2>;
     constexpr int N = F::N;
+    constexpr int NT = 2 * CC * F::T;
     extern __shared__ float2 sm[];
     float2* tw = sm;                        // [N]
     float2* MX = tw + N;                    // [N][CC] x multiplier at (ky, c)
     float2* MY = MX + N * CC;               // [N][CC]
-    float2* Z0 = MY + N * CC;               // transposes, [ZS][CC] each
-    float2* Z1 = Z0 + F::ZS * CC;
-    float2* Z2 = Z1 + F::ZS * CC;
-    float2* Z3 = Z2 + F::ZS * CC;
+    float2* Zf = MY + N * CC;               // forward transposes of the two threads' fields, [2][ZS][CC]
+    float2* Zi = Zf + 2 * F::ZS * CC;       // inverse transposes of the two outputs, [2][ZS][CC]
     const int k = blockIdx.y;
-    const int c = threadIdx.x % CC, idx = threadIdx.x / CC;
+    const int f = threadIdx.x / (CC * F::T);
+    const int tl = threadIdx.x - f * (CC * F::T);
+    const int c = tl % CC, idx = tl / CC;
     const int kx = blockIdx.x * CC + c;
     const bool colok = kx < g.hc;
     const int kxc = colok ? kx : g.hc - 1;
-    const bool two = mode != 0;
     const size_t base = size_t(k) * N * g.hp + kxc;
-    // prologue: tables into shared memory (independent of the preceding kernel) ...
-    constexpr int NT = CC * F::T;
     static_for<0, (N + NT - 1) / NT>([&](auto I) {
         const int i = decltype(I)::value * NT + threadIdx.x;
         if (i < N) tw[i] = g.tw[i];
@@ -123,58 +122,48 @@ __global__ void __launch_bounds__(CC * Fft2<N1, N2>::T) kf_col(Geo g, float2* __
             MY[i] = my;
         }
     });
-    // ... then the columns written by the preceding pass (A layout)
     pdl_wait_then_release();
-    float2 a0[N1], a1[N1];
+    float2* Zmine = Zf + f * F::ZS * CC + c;
+    float2 a[N1];
     if (idx < N2) {
+        const float2* src = (mode == 0 || f == 0) ? A : B;
         static_for<0, N1>([&](auto I) {
             constexpr int n1 = decltype(I)::value;
-            a0[n1] = A[base + size_t(N2 * n1 + idx) * g.hp];
-            if (two) a1[n1] = B[base + size_t(N2 * n1 + idx) * g.hp];
+            a[n1] = src[base + size_t(N2 * n1 + idx) * g.hp];
         });
     }
+    __syncthreads();   // twiddles and multipliers staged by all threads
+    if (idx < N2) F::template fwd_a<CC>(a, idx, Zmine, tw);
     __syncthreads();
-    if (idx < N2) {
-        F::template fwd_a<CC>(a0, idx, Z0 + c, tw);
-        if (two) F::template fwd_a<CC>(a1, idx, Z1 + c, tw);
-    }
-    __syncthreads();
+    float2 b[N2];
+    const float2* Mm = (f == 0) ? MX : MY;
     if (idx < N1) {
-        float2 b0[N2], b1[N2];
-        F::template fwd_b_load<CC>(b0, idx, Z0 + c);
-        if (two) F::template fwd_b_load<CC>(b1, idx, Z1 + c);
-        F::fwd_b(b0);
-        if (two) F::fwd_b(b1);
+        F::template fwd_b_load<CC>(b, idx, Zmine);
+        F::fwd_b(b);
         static_for<0, N2>([&](auto I) {
             constexpr int k2 = decltype(I)::value;
-            const int m = (idx + N1 * k2) * CC + c;
-            const float2 mx = MX[m], my = MY[m];
-            if (mode == 0) {
-                const float2 X = b0[k2];
-                b0[k2] = cmul(X, mx);
-                b1[k2] = cmul(X, my);
-            } else if (mode == 1) {
-                b0[k2] = cmul(b0[k2], mx);
-                b1[k2] = cmul(b1[k2], my);
-            } else {
-                b0[k2] = cadd(cmul(b0[k2], mx), cmul(b1[k2], my));
-            }
+            b[k2] = cmul(b[k2], Mm[(idx + N1 * k2) * CC + c]);
         });
-        F::template inv_b<CC>(b0, idx, Z2 + c, tw);
-        if (mode != 2) F::template inv_b<CC>(b1, idx, Z3 + c, tw);
+        if (mode == 2 && f == 1) {   // hand the product to the f = 0 thread of the same column
+            static_for<0, N2>([&](auto I) { Zi[((F::ZS + idx * N2 + decltype(I)::value) * CC) + c] = b[decltype(I)::value]; });
+        }
+    }
+    if (mode == 2) __syncthreads();
+    if (idx < N1 && (mode != 2 || f == 0)) {
+        if (mode == 2)
+            static_for<0, N2>([&](auto I) {
+                b[decltype(I)::value] = cadd(b[decltype(I)::value], Zi[((F::ZS + idx * N2 + decltype(I)::value) * CC) + c]);
+            });
+        F::template inv_b<CC>(b, idx, Zi + f * F::ZS * CC + c, tw);
     }
     __syncthreads();
-    if (idx < N2 && colok) {
-        F::template inv_a_load<CC>(a0, idx, Z2 + c);
-        F::inv_a(a0);
-        if (mode != 2) {
-            F::template inv_a_load<CC>(a1, idx, Z3 + c);
-            F::inv_a(a1);
-        }
+    if (idx < N2 && colok && (mode != 2 || f == 0)) {
+        F::template inv_a_load<CC>(a, idx, Zi + f * F::ZS * CC + c);
+        F::inv_a(a);
+        float2* dst = f == 0 ? A : B;
         static_for<0, N1>([&](auto I) {
             constexpr int n1 = decltype(I)::value;
-            A[base + size_t(idx + N2 * n1) * g.hp] = a0[n1];
-            if (mode != 2) B[base + size_t(idx + N2 * n1) * g.hp] = a1[n1];
+            dst[base + size_t(idx + N2 * n1) * g.hp] = a[n1];
         });
     }
 }
@@ -437,18 +426,22 @@ __global__ void __launch_bounds__(RR * Fft2<N1, N2>::T) kf_row_adj_rho(Geo g, fl
     const bool yin = yd >= 0 && yd < g.n;
     float* bx = rbx + row * N;
     float* by = rby + row * N;
-    // prologue: adjoint state, medium, PML, twiddles; after the wait the spectrum and the
-    // pressure history (the segment recompute that writes it may be the preceding kernel)
-    float s0[N1], s1[N1], cc[N1], hv[N1], fa[N1];
+    // prologue: adjoint state, dJ/dc accumulator, medium, PML, twiddles; after the wait the
+    // spectrum and the pressure history (the segment recompute that writes it may be the
+    // preceding kernel)
+    float s0[N1], s1[N1], cc[N1], hv[N1], fa[N1], cb[N1];
+    float* cbr = cbar + (size_t(k) * g.n + (yin ? yd : 0)) * g.n;
     if (aact) {
         const float* cr = medium_of(g, cg, k) + size_t(yy) * N;
         static_for<0, N1>([&](auto I) {
             constexpr int n1 = decltype(I)::value;
             const int x = idx + N2 * n1;
+            const int xd = x - g.P;
             s0[n1] = bx[x];
             s1[n1] = by[x];
             cc[n1] = cr[x];
             fa[n1] = g.a_cell[x];
+            cb[n1] = (yin && xd >= 0 && xd < g.n) ? cbr[xd] : 0.f;
         });
     }
     const float acy = g.a_cell[yy];
@@ -503,7 +496,7 @@ __global__ void __launch_bounds__(RR * Fft2<N1, N2>::T) kf_row_adj_rho(Geo g, fl
             const float vbx = s0[n1] + c2 * p_b;
             const float vby = s1[n1] + c2 * p_b;
             const int xd = x - g.P;
-            if (yin && xd >= 0 && xd < g.n) cbar[(size_t(k) * g.n + yd) * g.n + xd] += 2.f * hv[n1] * p_b / c;
+            if (yin && xd >= 0 && xd < g.n) cbr[xd] = cb[n1] + 2.f * hv[n1] * p_b / c;
             const float acx = fa[n1];
             const float tx = acx * vbx, ty = acy * vby;
             bx[x] = acx * tx;
@@ -541,6 +534,7 @@ template <int N1, int N2, int RR, int CC>
 struct FixedImpl {
     using F = Fft2<N1, N2>;
     static constexpr size_t smem_col = (F::N + 2 * F::N * CC + 4 * F::ZS * CC) * sizeof(float2);
+    static_assert(2 * F::ZS >= F::ZS + F::N1 * F::N2, "product hand-off fits the inverse buffer");
     static constexpr size_t smem_row = RowSmem<F, RR>::bytes;
 
     static int configure() {
@@ -559,7 +553,7 @@ struct FixedImpl {
     }
     static void col(const Geo& g, cudaStream_t st, float2* A, float2* B, int mode, int op, float scale) {
         dim3 grid((g.hc + CC - 1) / CC, g.K);
-        launch_pdl(kf_col<N1, N2, CC>, grid, dim3(CC * F::T), smem_col, st, true, g, A, B, mode, op, scale);
+        launch_pdl(kf_col<N1, N2, CC>, grid, dim3(2 * CC * F::T), smem_col, st, true, g, A, B, mode, op, scale);
     }
     static void row_u(const Geo& g, cudaStream_t st, float2* A, float2* B, float* ux, float* uy, int kind,
                       int init) {

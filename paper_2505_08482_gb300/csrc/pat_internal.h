@@ -47,7 +47,7 @@ struct Ws {
     double* J; double* part; int* flag;           // objective per instance, partial sums [K][32], flag
     // gradient only
     float* ckpt;                                  // [nseg-1][4][K][ng][ng]
-    float* hist;                                  // [K][s_eff][ng][ng] pressure history
+    float* hist;                                  // [2][K][s_eff][ng][ng] pressure history (two segments)
     float* ubx; float* uby; float* rbx; float* rby;  // adjoint state [K][ng][ng]
     float2* A2; float2* B2;                       // adjoint spectra
     float* cbar;                                  // [K][n][n]
@@ -90,11 +90,19 @@ struct pat_plan_s {
     };
     bool use_graphs;
     std::vector<Graph> graphs;
+    // second stream and events of the reverse sweep (recompute overlapped with the adjoint)
+    cudaStream_t side;
+    cudaEvent_t ev_start, ev_rec[2], ev_adj[2];
 };
 
 namespace pat {
 
 Ws resolve(const pat_plan_s* p, void* base, bool grad);
+
+// pressure history buffer of segment j (segments alternate between two buffers)
+inline float* hist_of(const pat_plan_s* p, const Ws& w, int j) {
+    return w.hist + size_t(j & 1) * p->K * p->s_eff * p->ng * p->ng;
+}
 
 // launch accounting / optional event timing of one kernel class (timing.cu)
 void count_launch();

@@ -113,7 +113,7 @@ static void layout(pat_plan_s* p) {
     p->o_flag = o; o = align256(o + 4 * sizeof(int));
     p->ws_fwd = o;
     p->o_ckpt = o; o = align256(o + size_t(std::max(p->nseg - 1, 0)) * 4 * f);
-    p->o_hist = o; o = align256(o + size_t(p->K) * p->s_eff * p->ng * p->ng * sizeof(float));
+    p->o_hist = o; o = align256(o + size_t(p->nseg > 1 ? 2 : 1) * p->K * p->s_eff * p->ng * p->ng * sizeof(float));
     p->o_adj = o; o = align256(o + 4 * f);
     p->o_A2 = o; o = align256(o + spec);
     p->o_B2 = o; o = align256(o + spec);
@@ -216,6 +216,8 @@ extern "C" int pat_plan_create_batched(pat_plan* out, const pat_grid* g, int m, 
     p->nseg = (g->nt + p->s_eff - 1) / p->s_eff;
     p->hist_valid_ws = nullptr;
     p->use_graphs = false;
+    p->side = nullptr;
+    p->ev_start = p->ev_rec[0] = p->ev_rec[1] = p->ev_adj[0] = p->ev_adj[1] = nullptr;
     cudaGetDevice(&p->device);
     radix_schedule(ng, &p->fft);
 
@@ -351,6 +353,16 @@ extern "C" int pat_plan_create_batched(pat_plan* out, const pat_grid* g, int m, 
         return rc;
     }
     layout(p);
+    if (cudaStreamCreateWithFlags(&p->side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&p->ev_start, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&p->ev_rec[0], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&p->ev_rec[1], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&p->ev_adj[0], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&p->ev_adj[1], cudaEventDisableTiming) != cudaSuccess) {
+        int rc2 = cuda_fail(cudaGetLastError(), "pat_plan_create (stream, events)");
+        pat_plan_destroy(p);
+        return rc2;
+    }
     *out = p;
     return PAT_OK;
 }
@@ -358,6 +370,12 @@ extern "C" int pat_plan_create_batched(pat_plan* out, const pat_grid* g, int m, 
 extern "C" void pat_plan_destroy(pat_plan p) {
     if (!p) return;
     for (auto& g : p->graphs) cudaGraphExecDestroy(g.exec);
+    for (cudaEvent_t e : {p->ev_start, p->ev_rec[0], p->ev_rec[1], p->ev_adj[0], p->ev_adj[1]})
+        if (e) cudaEventDestroy(e);
+    if (p->side) {
+        cudaStreamSynchronize(p->side);
+        cudaStreamDestroy(p->side);
+    }
     if (p->dev) cudaFree(p->dev);
     delete p;
 }
