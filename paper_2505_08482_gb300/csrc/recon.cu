@@ -255,7 +255,6 @@ int Batch::level(int li, const float* const* xprev, int nprev) {
             RC(vdot(st, s.ct, s.ct, nn, sc(i, S_CT), part));
         }
     }
-    const bool finest = li == cfg.nlevels - 1;
     RC(evaluate(true, false));
     for (int i = 0; i < ni; ++i) I[i].J = hJ[i];
     for (int it = 0; it < cfg.iters; ++it) {
@@ -417,7 +416,8 @@ int Batch::level(int li, const float* const* xprev, int nprev) {
             std::swap(s.g, s.gt);
             s.J = Jn;
             if (rel < cfg.rtol) s.active = false;
-            if (finest && s.ct && ins[i].ec_target > 0 && ec <= ins[i].ec_target) s.active = false;
+            // a tracked instance leaves a level (the last one: stops) once E_c reaches its target
+            if (s.ct && ins[i].ec_target > 0 && ec <= ins[i].ec_target) s.active = false;
         }
     }
     return PAT_OK;

@@ -259,8 +259,8 @@ def reconstruct_batched(cfg: ReconConfig, instances, stream=None, max_report=409
 
     ``instances``: list of dicts with device tensors ``y_meas`` [K][nt][m],
     ``w`` [K], ``c_init`` [N][N] and optional ``p0_init`` [K][N][N], ``c_true``
-    [N][N] (E_c per iteration) and ``ec_target`` (stop once E_c is reached on
-    the finest level).  Returns a list of (c, p0, report rows, status) and the
+    [N][N] (E_c per iteration) and ``ec_target`` (leave a level, the finest:
+    stop, once E_c is reached).  Returns a list of (c, p0, report rows, status) and the
     total wall time in ms.
     """
     N = int(cfg.levels[-1])

@@ -217,7 +217,7 @@ def init_params(levels, base, in_ch, seed=0) -> np.ndarray:
 
 
 def iterations_to(rows, target, nlevels):
-    """(iterations, ms) until E_c <= target on the finest level, or (None, None)."""
+    """(iterations over all levels, ms) until E_c <= target on the finest level, or (None, None)."""
     its, ms = 0, 0.0
     for r in rows:
         its += 1
