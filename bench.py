@@ -60,7 +60,7 @@ def bytes_per_cell(cls: int, ng: int, n: int, ckpt_hist: bool = True) -> float:
     return table[cls]
 
 
-KERNEL_FILES = ("fft.cuh", "fft2l.cuh", "geo.cuh", "kfixed.cuh", "kfixed_300.cu", "kernels.cu")
+KERNEL_FILES = ("fft.cuh", "fft2l.cuh", "geo.cuh", "kfixed.cuh", "kfixed_300.cu", "kernels.cu", "api.cu")
 
 
 def kernel_source_hash() -> str:
@@ -293,10 +293,11 @@ def run_ours(args, rank, world, local_rank):
     B.check(L.pat_timing_enable(0, 0, 1), "pat_timing_enable")
     dom = max(per_class, key=lambda c: per_class[c][0])
     per_eval_launches = per_class[dom][1]
-    # the dominant kernel's launch time: every 32nd launch bracketed by events, in eager mode
-    # (events inside a replayed graph are not per-launch timers); the timed region itself
-    # replays graphs unless --no-graphs
-    B.check(L.pat_timing_enable(dom, per_eval_launches * args.steps // 32 + 16, 32), "pat_timing_enable")
+    # the dominant kernel's launch time: every 32nd launch (every launch of a segment kernel)
+    # bracketed by events, in eager mode (events inside a replayed graph are not per-launch
+    # timers); the timed region itself replays graphs unless --no-graphs
+    every = 32 if per_eval_launches > 1000 else 1
+    B.check(L.pat_timing_enable(dom, per_eval_launches * args.steps // every + 16, every), "pat_timing_enable")
     for _ in range(args.steps):
         grad_eval()
     dom_ms, dom_cnt = ctypes_read(L)
@@ -396,7 +397,8 @@ def run_ours(args, rank, world, local_rank):
             "frac": achieved / peak, "traffic": stored_traffic(dom, src_hash),
             "peak_kind": f"{peak_kind} hbm_gbs", "algorithmic_bytes_per_launch": bpl,
             "avg_launch_us": avg_s * 1e6, "launches_timed": dom_cnt,
-            "sampling": "every 32nd launch over --steps eager evaluations after the warm-up",
+            "sampling": f"every {every}{'nd' if every == 32 else 'st'} launch over --steps eager evaluations "
+                        "after the warm-up",
             "share_of_step": (dom_ms / max(dom_cnt, 1)) * per_eval_launches / (t_ms / args.steps) if t_ms > 0 else None,
             "per_class_ms_per_eval_unsampled": {B.KERNEL_CLASSES[c]: round(v[0], 3) for c, v in per_class.items()}}
 
@@ -408,7 +410,7 @@ def run_ours(args, rank, world, local_rank):
             "grad_gcell_steps_per_s": value * ng * ng * K * (nt - 1) / 1e9,
             "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": launches, "roofline": roof, "clocks": clocks, "kernel_source_hash": src_hash,
-            "autotune_ms_per_step": {str(v): round(t, 4) for v, t in tuned.items()}, "variant": plan.variant,
+            "autotune_ms_per_grad_eval": {str(v): round(t, 2) for v, t in tuned.items()}, "variant": plan.variant,
             "cuda_graphs": not args.no_graphs}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         nt_s = args.cpu_sample_steps or 300

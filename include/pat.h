@@ -106,11 +106,18 @@ int pat_plan_shape(pat_plan plan, int* ninst, int* K);
 int pat_plan_ng(pat_plan plan);
 
 /* Kernel variants of a plan.  Grid sides with a compiled two-level FFT
- * (108, 144, 180, 200, 240, 300) have fixed-size passes in several tile
- * shapes (variant 0: 4 rows / 4 spectral columns per CTA, variant 1: 8 rows /
- * 2 columns); every side also has the generic shared-memory Stockham passes
- * (variant -1).  All variants compute the same scheme.  A new plan uses
- * variant 0 when it exists, else -1.  pat_plan_variants returns the number of
+ * (108, 144, 180, 200, 240, 300 = N1 x N2) have five fixed-size variants,
+ * all one launch per pass:
+ *   0  column and velocity passes on the N1 x N2 factorisation, density
+ *      passes on N2 x N1 (4 rows / 4 spectral columns per CTA);
+ *   1  all passes N1 x N2, 4 rows / 4 columns per CTA;
+ *   2  all passes N1 x N2, 8 rows / 2 columns per CTA;
+ *   3  as 1 with the row passes' state staged in shared memory by TMA bulk
+ *      copies instead of registers;
+ *   4  all passes N2 x N1, 4 rows / 4 columns per CTA.
+ * Every side also has the generic shared-memory Stockham passes (variant
+ * -1).  All variants compute the same scheme.  A new plan uses variant 0
+ * when it exists, else -1.  pat_plan_variants returns the number of
  * fixed-size variants; pat_plan_set_variant selects one (PAT_EINVAL if it
  * does not exist); pat_plan_variant returns the current one. */
 int pat_plan_variants(pat_plan plan);
@@ -125,12 +132,16 @@ int pat_plan_variant(pat_plan plan);
  * addresses for new data gets the new data.  enable = 0 frees the graphs. */
 int pat_plan_set_graphs(pat_plan plan, int enable);
 
-/* Autotuner: times a short run of forward steps with every variant of the
- * plan (generic and fixed-size tile shapes) on this GPU and keeps the
- * fastest.  d_ws: a forward workspace (NULL: a temporary one is allocated
- * and freed on the stream).  h_ms: host array of pat_plan_variants(plan)+1
- * entries (may be NULL) receiving the time per step of variants -1, 0, ...
- * in ms.  Synchronises the stream; with no fixed-size variant it selects -1. */
+/* Autotuner: times every variant of the plan (generic and fixed-size) on
+ * this GPU and keeps the fastest.  With a gradient workspace (ws_bytes >=
+ * PAT_WS_GRADIENT size) it times one whole gradient evaluation per variant
+ * (forward sweep with checkpoints, reverse sweep with the recompute stream;
+ * c = c_ref, p0 = 0, zero residual), otherwise 32 forward steps on a forward
+ * workspace (d_ws NULL: a temporary one is allocated and freed on the
+ * stream).  The workspace contents are overwritten.  h_ms: host array of
+ * pat_plan_variants(plan)+1 entries (may be NULL) receiving, for variants
+ * -1, 0, ..., the ms per gradient evaluation or per forward step.
+ * Synchronises the stream; with no fixed-size variant it selects -1. */
 int pat_plan_autotune(pat_plan plan, void* d_ws, size_t ws_bytes, double* h_ms, void* stream);
 
 /* Smallest PML width >= min_pml for which n + 2 P satisfies the grid rules
@@ -193,9 +204,13 @@ int pat_adjoint_grad(pat_plan plan, const float* d_c, const float* d_p0, const f
 int pat_vjp(pat_plan plan, const float* d_c, const float* d_p0, const float* d_ybar,
             float* d_grad_p0, float* d_grad_c, void* d_ws, size_t ws_bytes, void* stream);
 
-/* Non-finite flag of the last objective evaluated on this workspace:
- * copies it to *h_flag (1 if J or a residual was NaN/Inf) after
- * synchronising the stream. */
+/* Status of the last calls on this workspace, after synchronising the
+ * stream: *h_flag bit 0 (PAT_STATUS_NONFINITE) if the last objective met a
+ * NaN/Inf in J or a residual; bit 1 (PAT_STATUS_WAIT) if a kernel of the last
+ * pat_forward / pat_adjoint_grad / pat_vjp gave up a bounded wait for its
+ * staged copies (variant 3; the results of that call are then invalid). */
+#define PAT_STATUS_NONFINITE 1
+#define PAT_STATUS_WAIT 2
 int pat_status(pat_plan plan, const void* d_ws, int* h_flag, void* stream);
 
 /* ---- reconstruction (Sec. 3, Sec. 3.1) ---- */
@@ -309,7 +324,7 @@ typedef struct {
     int K;
     pat_report* report;
     const float* d_c_true;   /* optional [N][N]: report E_c per iteration */
-    double ec_target;        /* > 0 with d_c_true: stop once E_c <= ec_target on the finest level */
+    double ec_target;        /* > 0 with d_c_true: leave a level (the finest: stop) once E_c <= ec_target */
 } pat_instance;
 
 /* Several independent reconstructions that share cfg (levels, domain,

@@ -31,6 +31,8 @@ KERNEL_CLASSES = {1: "k_row_rho", 2: "k_row_u", 3: "k_col(grad)", 4: "k_col(pair
 PAT_WS_FORWARD = 0
 PAT_NOALLOC_SCRATCH_BYTES = 16 * 1024 * 1024
 PAT_WS_GRADIENT = 1
+PAT_STATUS_NONFINITE = 1
+PAT_STATUS_WAIT = 2
 
 
 class PatGrid(ctypes.Structure):

@@ -14,6 +14,7 @@
 #include <cstdint>
 
 #include "pat_internal.h"
+#include "vec.h"
 
 using namespace pat;
 
@@ -44,6 +45,15 @@ int step(const Launch& L, const Ws& w, int n, float* y, float* hist, int hist_sl
 
 size_t state_bytes(const pat_plan_s* p) { return 4 * size_t(p->K) * p->ng * p->ng * sizeof(float); }
 
+// forward steps n0 .. n1-1; p^{n+1} into hist slot n+1-hbase when hist and n+1 >= hbase
+int run_steps(const Launch& L, const Ws& w, int n0, int n1, float* y, float* hist, int hbase) {
+    for (int n = n0; n < n1; ++n) {
+        const bool h = hist && n + 1 >= hbase;
+        RC(step(L, w, n, y, h ? hist : nullptr, n + 1 - hbase));
+    }
+    return PAT_OK;
+}
+
 }  // namespace
 
 int pat::forward_sweep(pat_plan_s* p, const float* c, const float* p0, float* y, const Ws& w, bool keep,
@@ -51,16 +61,25 @@ int pat::forward_sweep(pat_plan_s* p, const float* c, const float* p0, float* y,
     Launch L{p, st};
     RC(launch_medium(L, c, w.cg));
     PAT_CUDA(cudaMemsetAsync(y, 0, size_t(p->K) * p->nt * p->m * sizeof(float), st));
+    PAT_CUDA(cudaMemsetAsync(w.flag + 1, 0, sizeof(int), st));   // bounded-wait status of this call
     const int last0 = (p->nseg - 1) * p->s_eff;
     float* hlast = keep ? hist_of(p, w, p->nseg - 1) : nullptr;
     RC(launch_row_rho(L, w, 1, p0, y, 0, (keep && last0 == 0) ? hlast : nullptr, 0));
-    for (int n = 0; n + 1 < p->nt; ++n) {
-        if (keep && n > 0 && n % p->s_eff == 0) {
-            PAT_CUDA(cudaMemcpyAsync(w.ckpt + size_t(n / p->s_eff - 1) * 4 * p->K * p->ng * p->ng, w.ux,
+    // segments of s steps with the state copied at their starts (one segment without checkpoints)
+    const int seg = keep ? p->s_eff : p->nt;
+    for (int n0 = 0; n0 + 1 < p->nt;) {
+        if (keep && n0 > 0) {
+            PAT_CUDA(cudaMemcpyAsync(w.ckpt + size_t(n0 / p->s_eff - 1) * 4 * p->K * p->ng * p->ng, w.ux,
                                      state_bytes(p), cudaMemcpyDeviceToDevice, st));
         }
-        const bool h = keep && (n + 1) >= last0;
-        RC(step(L, w, n, y, h ? hlast : nullptr, n + 1 - last0));
+        const int n1 = std::min(p->nt - 1, (n0 / seg + 1) * seg);
+        RC(run_steps(L, w, n0, n1, y, hlast, last0));
+        n0 = n1;
+    }
+    // a last segment that starts at level Nt-1 is restored from a checkpoint of that level
+    if (keep && p->nt > 1 && (p->nt - 1) % p->s_eff == 0) {
+        PAT_CUDA(cudaMemcpyAsync(w.ckpt + size_t((p->nt - 1) / p->s_eff - 1) * 4 * p->K * p->ng * p->ng, w.ux,
+                                 state_bytes(p), cudaMemcpyDeviceToDevice, st));
     }
     return PAT_OK;
 }
@@ -81,7 +100,18 @@ int recompute(pat_plan_s* p, const float* p0, const Ws& w, int j, cudaStream_t s
                                  st));
         RC(launch_row_rho(L, w, 2, nullptr, nullptr, 0, h, 0));
     }
-    for (int n = n0; n < n1; ++n) RC(step(L, w, n, nullptr, h, n + 1 - n0));
+    return run_steps(L, w, n0, n1, nullptr, h, n0);
+}
+
+// adjoint steps n_hi down to n_lo (first: n_hi is the first adjoint step of the sweep)
+int run_adj(const Launch& L, const Ws& w, const float* r, int n_hi, int n_lo, bool first, const float* h, int hbase,
+            float sg, float sd) {
+    for (int n = n_hi; n >= n_lo; --n) {
+        RC(launch_row_adj_rho(L, w, (first && n == n_hi) ? 1 : 0, r, n, h, n - hbase));
+        RC(launch_col(L, w.A2, w.B2, 1, 0, sg));
+        RC(launch_row_adj_u(L, w));
+        RC(launch_col(L, w.A2, w.B2, 2, 1, sd));
+    }
     return PAT_OK;
 }
 
@@ -115,13 +145,9 @@ int reverse_sweep(pat_plan_s* p, const float* p0, const float* r, float* grad_p0
         const int n1 = std::min(n0 + p->s_eff, p->nt) - 1;
         if (j < last || !hist_last_valid) PAT_CUDA(cudaStreamWaitEvent(st, p->ev_rec[j & 1], 0));
         const float* h = hist_of(p, w, j);
-        for (int n = n1; n >= std::max(n0, 1); --n) {
-            RC(launch_row_adj_rho(L, w, have_q ? 0 : 1, r, n, h, n - n0));
-            RC(launch_col(L, w.A2, w.B2, 1, 0, sg));
-            RC(launch_row_adj_u(L, w));
-            RC(launch_col(L, w.A2, w.B2, 2, 1, sd));
-            have_q = true;
-        }
+        const int lo = std::max(n0, 1);
+        RC(run_adj(L, w, r, n1, lo, !have_q, h, n0, sg, sd));
+        if (n1 >= lo) have_q = true;
         // segment j - 2 reuses this segment's buffer once its adjoint steps are done
         if (j - 2 >= 0) {
             PAT_CUDA(cudaEventRecord(p->ev_adj[j & 1], st));
@@ -240,6 +266,7 @@ extern "C" int pat_vjp(pat_plan p, const float* c, const float* p0, const float*
     Ws w = resolve(p, ws, true);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     Launch L{p, st};
+    PAT_CUDA(cudaMemsetAsync(w.flag + 1, 0, sizeof(int), st));   // bounded-wait status of this call
     RC(launch_medium(L, c, w.cg));
     const bool valid = (p->hist_valid_ws == ws);
     RC(reverse_sweep(p, p0, ybar, grad_p0, grad_c, w, valid, st));
@@ -247,6 +274,9 @@ extern "C" int pat_vjp(pat_plan p, const float* c, const float* p0, const float*
     return PAT_OK;
 }
 
+// Autotuner.  With a forward workspace it times forward steps; with a gradient workspace it
+// times whole gradient evaluations (forward sweep with checkpoints and the reverse sweep with
+// the recompute stream), since the variants differ in how the two streams share the SMs.
 extern "C" int pat_plan_autotune(pat_plan p, void* ws, size_t ws_bytes, double* h_ms, void* stream) {
     if (!p) { set_error("pat_plan_autotune: null plan"); return PAT_EINVAL; }
     const int nv = pat_plan_variants(p);
@@ -258,25 +288,45 @@ extern "C" int pat_plan_autotune(pat_plan p, void* ws, size_t ws_bytes, double* 
         ws = own;
         ws_bytes = p->ws_fwd;
     }
-    int rc = check_ws(p, ws, ws_bytes, false);
+    const bool grad = ws_bytes >= p->ws_grad;
+    int rc = check_ws(p, ws, ws_bytes, grad);
     cudaEvent_t e0 = nullptr, e1 = nullptr;
+    float* tmp = nullptr;   // gradient mode: c, p0, dJ/dp0, dJ/dc
+    const size_t nn = size_t(p->n) * p->n;
+    const size_t ntmp = 2 * (size_t(p->K) + p->ninst) * nn;
     double best = 1e300;
     int bestv = -1;
     if (rc == PAT_OK) {
-        // zero state and spectra; the timed steps then run on finite values
-        if (cudaMemsetAsync(ws, 0, p->ws_fwd, st) != cudaSuccess || cudaEventCreate(&e0) != cudaSuccess ||
-            cudaEventCreate(&e1) != cudaSuccess)
+        // zero state, spectra and residual; the timed passes then run on finite values
+        if (cudaMemsetAsync(ws, 0, grad ? p->ws_grad : p->ws_fwd, st) != cudaSuccess ||
+            cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
             rc = cuda_fail(cudaGetLastError(), "pat_plan_autotune");
     }
-    Ws w = resolve(p, ws, false);
+    if (rc == PAT_OK && grad) {
+        if (cudaMallocAsync(reinterpret_cast<void**>(&tmp), ntmp * sizeof(float), st) != cudaSuccess ||
+            cudaMemsetAsync(tmp, 0, ntmp * sizeof(float), st) != cudaSuccess)
+            rc = cuda_fail(cudaGetLastError(), "pat_plan_autotune buffers");
+        if (rc == PAT_OK) rc = vfill(st, tmp, float(p->g.c_ref), size_t(p->ninst) * nn);
+    }
+    Ws w = resolve(p, ws, grad);
     Launch L{p, st};
-    const int nsteps = 12;
+    float* c = tmp;
+    float* p0 = tmp ? tmp + size_t(p->ninst) * nn : nullptr;
+    float* gp0 = tmp ? p0 + size_t(p->K) * nn : nullptr;
+    float* gc = tmp ? gp0 + size_t(p->K) * nn : nullptr;
+    const int nsteps = 32;
     for (int v = -1; v < nv && rc == PAT_OK; ++v) {
         rc = select_variant(p, v);
-        for (int n = 1; n < 4 && rc == PAT_OK; ++n) rc = step(L, w, n, nullptr, nullptr, 0);
+        if (rc != PAT_OK) break;
+        rc = run_steps(L, w, 1, 4, nullptr, nullptr, 0);   // first launches of the variant's kernels
         if (rc != PAT_OK) break;
         cudaEventRecord(e0, st);
-        for (int n = 1; n <= nsteps && rc == PAT_OK; ++n) rc = step(L, w, n, nullptr, nullptr, 0);
+        if (grad) {
+            rc = forward_sweep(p, c, p0, w.ypred, w, true, st);
+            if (rc == PAT_OK) rc = reverse_sweep(p, p0, w.resid, gp0, gc, w, true, st);
+        } else {
+            rc = run_steps(L, w, 1, 1 + nsteps, nullptr, nullptr, 0);
+        }
         cudaEventRecord(e1, st);
         if (rc != PAT_OK) break;
         float ms = 0.f;
@@ -284,15 +334,17 @@ extern "C" int pat_plan_autotune(pat_plan p, void* ws, size_t ws_bytes, double* 
             rc = cuda_fail(cudaGetLastError(), "pat_plan_autotune timing");
             break;
         }
-        const double per = double(ms) / nsteps;
+        const double per = grad ? double(ms) : double(ms) / nsteps;
         if (h_ms) h_ms[v + 1] = per;
         if (per < best) {
             best = per;
             bestv = v;
         }
     }
+    p->hist_valid_ws = nullptr;
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
+    if (tmp) cudaFreeAsync(tmp, st);
     if (own) cudaFreeAsync(own, st);
     if (rc != PAT_OK) return rc;
     return select_variant(p, bestv);
@@ -302,7 +354,9 @@ extern "C" int pat_status(pat_plan p, const void* ws, int* h_flag, void* stream)
     if (!p || !ws || !h_flag) { set_error("pat_status: null argument"); return PAT_EINVAL; }
     const char* b = static_cast<const char*>(ws);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    PAT_CUDA(cudaMemcpyAsync(h_flag, b + p->o_flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+    int f[2] = {0, 0};
+    PAT_CUDA(cudaMemcpyAsync(f, b + p->o_flag, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
     PAT_CUDA(cudaStreamSynchronize(st));
+    *h_flag = (f[0] ? 1 : 0) | (f[1] ? 2 : 0);
     return PAT_OK;
 }

@@ -22,6 +22,6 @@ const FixedOps* fixed_ops_for(int ng, int v) {
     }
 }
 
-int fixed_variants(int ng) { return fixed_ops_for(ng, 0) ? 2 : 0; }
+int fixed_variants(int ng) { return fixed_ops_for(ng, 0) ? 5 : 0; }
 
 }  // namespace pat

@@ -22,6 +22,7 @@ struct Geo {
     const int2* sent;
     const float4* sentw;
     const int* kinst;    // instance of each data set (selects its c)
+    int* status;         // workspace status word of bounded waits (nullptr: not reported)
 };
 
 inline Geo geo(const pat_plan_s* p) {
@@ -33,6 +34,7 @@ inline Geo geo(const pat_plan_s* p) {
     g.a_cell = p->t.a_cell; g.a_stag = p->t.a_stag;
     g.srow = p->t.srow; g.sent = p->t.sent; g.sentw = p->t.sentw;
     g.kinst = p->t.kinst;
+    g.status = nullptr;
     return g;
 }
 

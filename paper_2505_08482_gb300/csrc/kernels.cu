@@ -533,7 +533,7 @@ __global__ void k_sum_partials(const double* __restrict__ part, const int* __res
 // ---------------------------------------------------------------------------
 // launchers
 
-static int check_launch(const char* what) {
+int check_launch(const char* what) {
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, what);
     return PAT_OK;
@@ -589,6 +589,13 @@ int select_variant(pat_plan_s* p, int variant) {
     return PAT_OK;
 }
 
+// plan constants plus the workspace's status word (second int of the flag region)
+static Geo geo_ws(const pat_plan_s* p, const Ws& w) {
+    Geo g = geo(p);
+    g.status = w.flag + 1;
+    return g;
+}
+
 static dim3 row_grid(const pat_plan_s* p) { return dim3((p->ng + p->R - 1) / p->R, p->K); }
 
 int launch_medium(const Launch& L, const float* c_dom, float* cg) {
@@ -605,7 +612,7 @@ int launch_row_rho(const Launch& L, const Ws& w, int mode, const float* p0, floa
     const pat_plan_s* p = L.p;
     prof_begin(PAT_K_ROW_RHO, L.st);
     if (p->fast)
-        p->fast->row_rho(geo(p), L.st, w.A, w.B, w.rx, w.ry, w.cg, mode, p0, y, tstep, hist, hist_slot);
+        p->fast->row_rho(geo_ws(p, w), L.st, w.A, w.B, w.rx, w.ry, w.cg, mode, p0, y, tstep, hist, hist_slot);
     else
         k_row_rho<<<row_grid(p), 256, p->smem_row, L.st>>>(geo(p), w.A, w.B, w.rx, w.ry, w.cg, mode, p0, y,
                                                            tstep, hist, hist_slot, p->R);
@@ -617,7 +624,7 @@ int launch_row_u(const Launch& L, const Ws& w, int init) {
     const pat_plan_s* p = L.p;
     prof_begin(PAT_K_ROW_U, L.st);
     if (p->fast)
-        p->fast->row_u(geo(p), L.st, w.A, w.B, w.ux, w.uy, 0, init);
+        p->fast->row_u(geo_ws(p, w), L.st, w.A, w.B, w.ux, w.uy, 0, init);
     else
         k_row_u<<<row_grid(p), 256, p->smem_row, L.st>>>(geo(p), w.A, w.B, w.ux, w.uy, init, p->R);
     prof_end(PAT_K_ROW_U, L.st);
@@ -642,7 +649,7 @@ int launch_row_adj_rho(const Launch& L, const Ws& w, int first, const float* res
     const pat_plan_s* p = L.p;
     prof_begin(PAT_K_ROW_ADJ_RHO, L.st);
     if (p->fast)
-        p->fast->row_adj_rho(geo(p), L.st, w.A2, w.B2, w.rbx, w.rby, w.cbar, w.cg, first, resid, tstep, hist,
+        p->fast->row_adj_rho(geo_ws(p, w), L.st, w.A2, w.B2, w.rbx, w.rby, w.cbar, w.cg, first, resid, tstep, hist,
                              hist_slot);
     else
         k_row_adj_rho<<<row_grid(p), 256, p->smem_row, L.st>>>(geo(p), w.A2, w.B2, w.rbx, w.rby, w.cbar, w.cg,
@@ -655,7 +662,7 @@ int launch_row_adj_u(const Launch& L, const Ws& w) {
     const pat_plan_s* p = L.p;
     prof_begin(PAT_K_ROW_ADJ_U, L.st);
     if (p->fast)
-        p->fast->row_u(geo(p), L.st, w.A2, w.B2, w.ubx, w.uby, 1, 0);
+        p->fast->row_u(geo_ws(p, w), L.st, w.A2, w.B2, w.ubx, w.uby, 1, 0);
     else
         k_row_adj_u<<<row_grid(p), 256, p->smem_row, L.st>>>(geo(p), w.A2, w.B2, w.ubx, w.uby, p->R);
     prof_end(PAT_K_ROW_ADJ_U, L.st);

@@ -13,9 +13,18 @@
 // adjoint terms); the forward transform of the updated fields goes back
 // through one transpose and a last shared-memory pass splits the two packed
 // half spectra.  Results are the same as the generic Stockham passes.
+//
+// The pointwise update needs the CTA's rows of the state, the medium and the
+// PML factors.  They are fetched before the programmatic-dependency wait so that
+// their latency overlaps the preceding kernel and the inverse transform: into
+// registers (STAGE = false) or, with STAGE = true, by TMA bulk copies into
+// shared memory (the RR rows of a data set are contiguous: one copy per array),
+// which leaves the registers to the FFT so that more CTAs share an SM.
 #pragma once
 
 #include <cuda_runtime.h>
+
+#include <cstdint>
 
 #include "fft2l.cuh"
 #include "geo.cuh"
@@ -38,12 +47,55 @@ struct FixedOps {
 const FixedOps* fixed_ops_for(int ng, int variant);   // nullptr if no fixed size matches
 int fixed_variants(int ng);                           // number of tile variants for ng (0 if none)
 
+// L2 load of a spectrum element (written by other CTAs of the preceding kernel)
+__device__ __forceinline__ float2 ld_spec(const float2* p) { return __ldcg(p); }
+
 // ---------------------------------------------------------------------------
-template <class F>
-__device__ __forceinline__ void load_twiddles_n(float2* tw, const Geo& g) {
-    for (int i = threadIdx.x; i < F::N; i += blockDim.x) tw[i] = g.tw[i];
+// TMA bulk copies global -> shared completing on an mbarrier.  Sources,
+// destinations and sizes are multiples of 16 bytes.
+__device__ __forceinline__ uint32_t s_addr(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* mb, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(s_addr(mb)), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+// one arrival that also announces `bytes` of copies to come
+__device__ __forceinline__ void mbar_arrive_expect(uint64_t* mb, uint32_t bytes) {
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(
+                     s_addr(mb)),
+                 "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* mb) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     s_addr(dst)),
+                 "l"(src), "r"(bytes), "r"(s_addr(mb))
+                 : "memory");
+}
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// Wait for phase `parity` of mb for at most limit_ns of wall time; on giving up the
+// status word gets bit 1 (PAT_STATUS_WAIT of pat_status) and the caller goes on.
+__device__ __forceinline__ void mbar_wait(uint64_t* mb, uint32_t parity, int* status,
+                                          uint64_t limit_ns = 2000000000ull) {
+    uint32_t done = 0;
+    const uint64_t t0 = global_ns();
+    for (;;) {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(s_addr(mb)), "r"(parity)
+            : "memory");
+        if (done || global_ns() - t0 > limit_ns) break;
+    }
+    if (!done && status) atomicOr(status, 2);
 }
 
+// ---------------------------------------------------------------------------
 // B layout of the packed inverse: b[k2] = Z[k1 + N1 k2] where Z is the full
 // spectrum of a + i b built from the half spectra rows ra (of a) and rb (of b).
 template <class F>
@@ -54,7 +106,7 @@ __device__ __forceinline__ void load_c2r_b(float2 (&b)[F::N2], int k1, const flo
         const int kx = k1 + F::N1 * k2;
         float2 z;
         if (2 * kx <= F::N) {
-            float2 a = ra[kx], bb = rb[kx];
+            float2 a = ld_spec(ra + kx), bb = ld_spec(rb + kx);
             if (kx == 0 || 2 * kx == F::N) {
                 a.y = 0.f;
                 bb.y = 0.f;
@@ -62,7 +114,7 @@ __device__ __forceinline__ void load_c2r_b(float2 (&b)[F::N2], int k1, const flo
             z = make_float2(a.x - bb.y, a.y + bb.x);
         } else {
             const int kk = F::N - kx;
-            const float2 a = ra[kk], bb = rb[kk];
+            const float2 a = ld_spec(ra + kk), bb = ld_spec(rb + kk);
             z = make_float2(a.x + bb.y, bb.x - a.y);
         }
         b[k2] = z;
@@ -85,7 +137,7 @@ __device__ __forceinline__ void col_mults(const Geo& g, int kx, int ky, int op, 
 // ---------------------------------------------------------------------------
 // column pass; mode 0: A -> (MX A, MY A) into (A, B); 1: (A, B) -> (MX A, MY B); 2: MX A + MY B -> A.
 // The two fields (or the two outputs) of a column are handled by separate threads (f = 0, 1).
-// Tables and twiddles are loaded before the dependency wait, the columns after it.
+// Tables and twiddles are staged before the dependency wait, the columns read after it.
 template <int N1, int N2, int CC>
 __global__ void __launch_bounds__(2 * CC * Fft2<N1, N2>::T) kf_col(Geo g, float2* __restrict__ A,
                                                                   float2* __restrict__ B, int mode, int op,
@@ -129,7 +181,7 @@ __global__ void __launch_bounds__(2 * CC * Fft2<N1, N2>::T) kf_col(Geo g, float2
         const float2* src = (mode == 0 || f == 0) ? A : B;
         static_for<0, N1>([&](auto I) {
             constexpr int n1 = decltype(I)::value;
-            a[n1] = src[base + size_t(N2 * n1 + idx) * g.hp];
+            a[n1] = ld_spec(src + base + size_t(N2 * n1 + idx) * g.hp);
         });
     }
     __syncthreads();   // twiddles and multipliers staged by all threads
@@ -197,16 +249,28 @@ __device__ __forceinline__ void finish_fwd(float2* Zs, int idx, bool active) {
     __syncthreads();
 }
 
-// Shared memory of the row passes: twiddles, two transpose buffers of RR rows, RR real rows.
+// Shared memory of the row passes: twiddles, two transpose buffers and RR real rows
+// (base); staged: then ns arrays of RR rows, the PML factors, nc arrays of RR domain
+// rows of width n, and the mbarrier.
 template <class F, int RR>
 struct RowSmem {
-    static constexpr size_t bytes = (F::N + 2 * RR * F::ZS) * sizeof(float2) + RR * F::N * sizeof(float);
+    static constexpr size_t base = (F::N + 2 * RR * F::ZS) * sizeof(float2) + RR * F::N * sizeof(float);
+    static constexpr size_t staged(int ns, int nc, int n) {
+        return base + (size_t(ns) * RR + 1) * F::N * sizeof(float) + size_t(nc) * RR * n * sizeof(float) + 16;
+    }
 };
+
+// bytes of nr consecutive rows of an Ng-wide field
+template <int N>
+__device__ __forceinline__ uint32_t rows_bytes(int nr) {
+    return uint32_t(nr) * N * sizeof(float);
+}
 
 // ---------------------------------------------------------------------------
 // velocity row pass; kind 0 forward: u <- a'(a' u - g) (init: u = g/2 first),
 // kind 1 adjoint: t' = a'(ub + g), ub <- a' t'.  Then (A, B) <- R2C of the new pair.
-template <int N1, int N2, int RR>
+// The state and PML factors are not written by the preceding kernel: fetched before the wait.
+template <int N1, int N2, int RR, bool STAGE>
 __global__ void __launch_bounds__(RR * Fft2<N1, N2>::T) kf_row_u(Geo g, float2* __restrict__ A,
                                                                 float2* __restrict__ B, float* __restrict__ ux,
                                                                 float* __restrict__ uy, int kind, int init) {
@@ -216,6 +280,10 @@ __global__ void __launch_bounds__(RR * Fft2<N1, N2>::T) kf_row_u(Geo g, float2* 
     float2* tw = sm;
     float2* Z0 = sm + N;
     float2* Z1 = Z0 + RR * F::ZS;
+    float* Sx = reinterpret_cast<float*>(Z1 + RR * F::ZS) + RR * N;   // staged u_x, u_y [RR][N] (after base)
+    float* Sy = Sx + RR * N;
+    float* Sa = Sy + RR * N;                                           // PML factors [N]
+    uint64_t* mb = reinterpret_cast<uint64_t*>(Sa + N);
     const int k = blockIdx.y, y0 = blockIdx.x * RR;
     const int r = threadIdx.x / T, idx = threadIdx.x % T;
     const int nr = min(RR, N - y0);
@@ -225,15 +293,26 @@ __global__ void __launch_bounds__(RR * Fft2<N1, N2>::T) kf_row_u(Geo g, float2* 
     const int yy = y0 + min(r, nr - 1);
     float* uxr = ux + row * N;
     float* uyr = uy + row * N;
-    // prologue: state and PML factors (A layout) and twiddles, which the preceding
-    // kernel does not write, then the spectra (B layout) after the dependency wait
+    const bool zero = kind == 0 && init;
     float sx[N1], sy[N1], fa[N1];
-    if (aact) {
+    if constexpr (STAGE) {
+        if (threadIdx.x == 0) {
+            const size_t r0 = (size_t(k) * N + y0) * N;
+            const uint32_t bytes = rows_bytes<N>(nr);
+            mbar_init(mb, 1);
+            mbar_arrive_expect(mb, (zero ? 0u : 2u * bytes) + uint32_t(N * sizeof(float)));
+            if (!zero) {
+                bulk_load(Sx, ux + r0, bytes, mb);
+                bulk_load(Sy, uy + r0, bytes, mb);
+            }
+            bulk_load(Sa, g.a_stag, N * sizeof(float), mb);
+        }
+    } else if (aact) {
         static_for<0, N1>([&](auto I) {
             constexpr int n1 = decltype(I)::value;
             const int x = idx + N2 * n1;
-            sx[n1] = (kind == 0 && init) ? 0.f : uxr[x];
-            sy[n1] = (kind == 0 && init) ? 0.f : uyr[x];
+            sx[n1] = zero ? 0.f : uxr[x];
+            sy[n1] = zero ? 0.f : uyr[x];
             fa[n1] = g.a_stag[x];
         });
     }
@@ -245,6 +324,7 @@ __global__ void __launch_bounds__(RR * Fft2<N1, N2>::T) kf_row_u(Geo g, float2* 
     __syncthreads();
     if (bact) F::inv_b(b, idx, Z0 + r * F::ZS, tw);
     __syncthreads();
+    if constexpr (STAGE) mbar_wait(mb, 0, g.status);
     if (aact) {
         float2 a[N1];
         F::inv_a_load(a, idx, Z0 + r * F::ZS);
@@ -253,18 +333,27 @@ __global__ void __launch_bounds__(RR * Fft2<N1, N2>::T) kf_row_u(Geo g, float2* 
             constexpr int n1 = decltype(I)::value;
             const int x = idx + N2 * n1;
             const float2 gv = a[n1];
-            const float ax = fa[n1];
+            float ax, ux0, uy0;
+            if constexpr (STAGE) {
+                ax = Sa[x];
+                ux0 = zero ? 0.f : Sx[r * N + x];
+                uy0 = zero ? 0.f : Sy[r * N + x];
+            } else {
+                ax = fa[n1];
+                ux0 = sx[n1];
+                uy0 = sy[n1];
+            }
             if (kind == 0) {
-                const float uxo = init ? 0.5f * gv.x : sx[n1];
-                const float uyo = init ? 0.5f * gv.y : sy[n1];
+                const float uxo = init ? 0.5f * gv.x : ux0;
+                const float uyo = init ? 0.5f * gv.y : uy0;
                 const float uxn = ax * (ax * uxo - gv.x);
                 const float uyn = ay * (ay * uyo - gv.y);
                 uxr[x] = uxn;
                 uyr[x] = uyn;
                 a[n1] = make_float2(uxn, uyn);
             } else {
-                const float tpx = ax * (sx[n1] + gv.x);
-                const float tpy = ay * (sy[n1] + gv.y);
+                const float tpx = ax * (ux0 + gv.x);
+                const float tpy = ay * (uy0 + gv.y);
                 uxr[x] = ax * tpx;
                 uyr[x] = ay * tpy;
                 a[n1] = make_float2(tpx, tpy);
@@ -279,8 +368,9 @@ __global__ void __launch_bounds__(RR * Fft2<N1, N2>::T) kf_row_u(Geo g, float2* 
 }
 
 // density / pressure row pass (mode 0 regular, 1 init from p0, 2 restore), sensor gather,
-// history, then A <- R2C of p (two rows per complex transform)
-template <int N1, int N2, int RR>
+// history, then A <- R2C of p (two rows per complex transform).  State, medium and PML are
+// written two or more kernels earlier: fetched before the wait.
+template <int N1, int N2, int RR, bool STAGE>
 __global__ void __launch_bounds__(RR * Fft2<N1, N2>::T) kf_row_rho(Geo g, float2* __restrict__ A,
                                                                   const float2* __restrict__ B,
                                                                   float* __restrict__ rx, float* __restrict__ ry,
@@ -295,6 +385,11 @@ __global__ void __launch_bounds__(RR * Fft2<N1, N2>::T) kf_row_rho(Geo g, float2
     float2* Z0 = sm + N;
     float2* Z1 = Z0 + RR * F::ZS;
     float* P = reinterpret_cast<float*>(Z1 + RR * F::ZS);   // [RR][N]
+    float* Sx = P + RR * N;                                 // staged rho_x, rho_y, c [RR][N] each
+    float* Sy = Sx + RR * N;
+    float* Sc = Sy + RR * N;
+    float* Sa = Sc + RR * N;                                // PML factors [N]
+    uint64_t* mb = reinterpret_cast<uint64_t*>(Sa + N);
     const int k = blockIdx.y, y0 = blockIdx.x * RR;
     const int r = threadIdx.x / T, idx = threadIdx.x % T;
     const int nr = min(RR, N - y0);
@@ -305,23 +400,34 @@ __global__ void __launch_bounds__(RR * Fft2<N1, N2>::T) kf_row_rho(Geo g, float2
     float* rxr = rx + row * N;
     float* ryr = ry + row * N;
     const float* cr = medium_of(g, cg, k) + size_t(yy) * N;
-    // prologue: state, medium, PML (written two or more kernels earlier), twiddles
+    const int yd = yy - g.P;
+    // initial pressure at x = idx + N2 n1 (mode 1)
+    auto p0_at = [&](int x) {
+        const int xd = x - g.P;
+        return (xd >= 0 && xd < g.n && yd >= 0 && yd < g.n) ? p0[(size_t(k) * g.n + yd) * g.n + xd] : 0.f;
+    };
     float s0[N1], s1[N1], cc[N1], fa[N1];
-    if (aact) {
-        const int yd = yy - g.P;
+    if constexpr (STAGE) {
+        if (threadIdx.x == 0) {
+            const size_t r0 = (size_t(k) * N + y0) * N;
+            const uint32_t bytes = rows_bytes<N>(nr);
+            mbar_init(mb, 1);
+            mbar_arrive_expect(mb, (mode == 1 ? 1u : 3u) * bytes + uint32_t(N * sizeof(float)));
+            if (mode != 1) {
+                bulk_load(Sx, rx + r0, bytes, mb);
+                bulk_load(Sy, ry + r0, bytes, mb);
+            }
+            bulk_load(Sc, medium_of(g, cg, k) + size_t(y0) * N, bytes, mb);
+            bulk_load(Sa, g.a_cell, N * sizeof(float), mb);
+        }
+    } else if (aact) {
         static_for<0, N1>([&](auto I) {
             constexpr int n1 = decltype(I)::value;
             const int x = idx + N2 * n1;
             cc[n1] = cr[x];
             fa[n1] = g.a_cell[x];
-            if (mode == 1) {
-                const int xd = x - g.P;
-                s0[n1] = (xd >= 0 && xd < g.n && yd >= 0 && yd < g.n) ? p0[(size_t(k) * g.n + yd) * g.n + xd] : 0.f;
-                s1[n1] = 0.f;
-            } else {
-                s0[n1] = rxr[x];
-                s1[n1] = ryr[x];
-            }
+            s0[n1] = mode == 1 ? p0_at(x) : rxr[x];
+            s1[n1] = mode == 1 ? 0.f : ryr[x];
         });
     }
     const float acy = g.a_cell[yy];
@@ -332,6 +438,7 @@ __global__ void __launch_bounds__(RR * Fft2<N1, N2>::T) kf_row_rho(Geo g, float2
     __syncthreads();
     if (bact) F::inv_b(b, idx, Z0 + r * F::ZS, tw);
     __syncthreads();
+    if constexpr (STAGE) mbar_wait(mb, 0, g.status);
     if (aact) {
         float* Pr = P + r * N;
         float* hr = hist ? hist + (size_t(k) * g.s_eff + hist_slot) * N * N + size_t(yy) * N : nullptr;
@@ -343,23 +450,33 @@ __global__ void __launch_bounds__(RR * Fft2<N1, N2>::T) kf_row_rho(Geo g, float2
         static_for<0, N1>([&](auto I) {
             constexpr int n1 = decltype(I)::value;
             const int x = idx + N2 * n1;
-            const float c = cc[n1];
+            float c, acx, v0, v1;
+            if constexpr (STAGE) {
+                c = Sc[r * N + x];
+                acx = Sa[x];
+                v0 = mode == 1 ? p0_at(x) : Sx[r * N + x];
+                v1 = mode == 1 ? 0.f : Sy[r * N + x];
+            } else {
+                c = cc[n1];
+                acx = fa[n1];
+                v0 = s0[n1];
+                v1 = s1[n1];
+            }
             float pv;
             if (mode == 0) {
                 const float2 gv = a[n1];
-                const float acx = fa[n1];
-                const float rxn = acx * (acx * s0[n1] - gv.x);
-                const float ryn = acy * (acy * s1[n1] - gv.y);
+                const float rxn = acx * (acx * v0 - gv.x);
+                const float ryn = acy * (acy * v1 - gv.y);
                 rxr[x] = rxn;
                 ryr[x] = ryn;
                 pv = c * c * (rxn + ryn);
             } else if (mode == 1) {
-                pv = s0[n1];
+                pv = v0;
                 const float rv = pv / (2.f * c * c);
                 rxr[x] = rv;
                 ryr[x] = rv;
             } else {
-                pv = c * c * (s0[n1] + s1[n1]);
+                pv = c * c * (v0 + v1);
             }
             Pr[x] = pv;
             if (hr) hr[x] = pv;
@@ -395,8 +512,10 @@ __global__ void __launch_bounds__(RR * Fft2<N1, N2>::T) kf_row_rho(Geo g, float2
 }
 
 // adjoint density row pass: pb = C2R(Q) + S^T r^n; rb += c^2 pb; cbar += 2 p pb / c;
-// t = a rb; rb <- a t; (A2, B2) <- R2C(t_x, t_y)
-template <int N1, int N2, int RR>
+// t = a rb; rb <- a t; (A2, B2) <- R2C(t_x, t_y).  Adjoint state, dJ/dc accumulator,
+// medium and PML are fetched before the wait; the spectrum and the pressure history (the
+// segment recompute that writes it may be the preceding kernel) after it.
+template <int N1, int N2, int RR, bool STAGE>
 __global__ void __launch_bounds__(RR * Fft2<N1, N2>::T) kf_row_adj_rho(Geo g, float2* __restrict__ A2,
                                                                       float2* __restrict__ B2,
                                                                       float* __restrict__ rbx,
@@ -413,6 +532,13 @@ __global__ void __launch_bounds__(RR * Fft2<N1, N2>::T) kf_row_adj_rho(Geo g, fl
     float2* Z0 = sm + N;
     float2* Z1 = Z0 + RR * F::ZS;
     float* PB = reinterpret_cast<float*>(Z1 + RR * F::ZS);   // [RR][N]
+    float* Sx = PB + RR * N;                                 // staged rb_x, rb_y, c, p history [RR][N] each
+    float* Sy = Sx + RR * N;
+    float* Sc = Sy + RR * N;
+    float* Sh = Sc + RR * N;
+    float* Sa = Sh + RR * N;                                 // PML factors [N]
+    float* Sb = Sa + N;                                      // dJ/dc rows of the domain [RR][n]
+    uint64_t* mb = reinterpret_cast<uint64_t*>(Sb + RR * g.n);
     const int k = blockIdx.y, y0 = blockIdx.x * RR;
     const int r = threadIdx.x / T, idx = threadIdx.x % T;
     const int nr = min(RR, N - y0);
@@ -426,13 +552,26 @@ __global__ void __launch_bounds__(RR * Fft2<N1, N2>::T) kf_row_adj_rho(Geo g, fl
     const bool yin = yd >= 0 && yd < g.n;
     float* bx = rbx + row * N;
     float* by = rby + row * N;
-    // prologue: adjoint state, dJ/dc accumulator, medium, PML, twiddles; after the wait the
-    // spectrum and the pressure history (the segment recompute that writes it may be the
-    // preceding kernel)
-    float s0[N1], s1[N1], cc[N1], hv[N1], fa[N1], cb[N1];
     float* cbr = cbar + (size_t(k) * g.n + (yin ? yd : 0)) * g.n;
-    if (aact) {
-        const float* cr = medium_of(g, cg, k) + size_t(yy) * N;
+    const float* cr = medium_of(g, cg, k) + size_t(yy) * N;
+    // domain rows of the tile in dJ/dc (staged when a row is a multiple of 16 bytes)
+    const int d0 = max(y0 - g.P, 0), d1 = min(y0 + nr - g.P, g.n);
+    const bool cb_staged = STAGE && (g.n % 4) == 0;
+    float s0[N1], s1[N1], cc[N1], hv[N1], fa[N1], cb[N1];
+    if constexpr (STAGE) {
+        if (threadIdx.x == 0) {
+            const size_t r0 = (size_t(k) * N + y0) * N;
+            const uint32_t bytes = rows_bytes<N>(nr);
+            const uint32_t cbytes = (cb_staged && d1 > d0) ? uint32_t(d1 - d0) * g.n * sizeof(float) : 0u;
+            mbar_init(mb, 2);   // this arrival and the history's after the wait
+            mbar_arrive_expect(mb, 3u * bytes + uint32_t(N * sizeof(float)) + cbytes);
+            bulk_load(Sx, rbx + r0, bytes, mb);
+            bulk_load(Sy, rby + r0, bytes, mb);
+            bulk_load(Sc, medium_of(g, cg, k) + size_t(y0) * N, bytes, mb);
+            bulk_load(Sa, g.a_cell, N * sizeof(float), mb);
+            if (cbytes) bulk_load(Sb, cbar + (size_t(k) * g.n + d0) * g.n, cbytes, mb);
+        }
+    } else if (aact) {
         static_for<0, N1>([&](auto I) {
             constexpr int n1 = decltype(I)::value;
             const int x = idx + N2 * n1;
@@ -449,8 +588,14 @@ __global__ void __launch_bounds__(RR * Fft2<N1, N2>::T) kf_row_adj_rho(Geo g, fl
     if (first)
         for (int i = threadIdx.x; i < RR * N; i += blockDim.x) PB[i] = 0.f;
     pdl_wait_then_release();
-    if (aact) {
-        const float* hr = hist + (size_t(k) * g.s_eff + hist_slot) * N * N + size_t(yy) * N;
+    const float* hr = hist + (size_t(k) * g.s_eff + hist_slot) * N * N + size_t(yy) * N;
+    if constexpr (STAGE) {
+        if (threadIdx.x == 0) {
+            const uint32_t bytes = rows_bytes<N>(nr);
+            mbar_arrive_expect(mb, bytes);
+            bulk_load(Sh, hist + (size_t(k) * g.s_eff + hist_slot) * N * N + size_t(y0) * N, bytes, mb);
+        }
+    } else if (aact) {
         static_for<0, N1>([&](auto I) { hv[decltype(I)::value] = hr[idx + N2 * decltype(I)::value]; });
     }
     float2 b[N2];
@@ -485,19 +630,35 @@ __global__ void __launch_bounds__(RR * Fft2<N1, N2>::T) kf_row_adj_rho(Geo g, fl
         }
     }
     __syncthreads();
+    if constexpr (STAGE) mbar_wait(mb, 0, g.status);
     if (aact) {
         float2 a[N1];
         static_for<0, N1>([&](auto I) {
             constexpr int n1 = decltype(I)::value;
             const int x = idx + N2 * n1;
-            const float p_b = PB[r * N + x];
-            const float c = cc[n1];
-            const float c2 = c * c;
-            const float vbx = s0[n1] + c2 * p_b;
-            const float vby = s1[n1] + c2 * p_b;
             const int xd = x - g.P;
-            if (yin && xd >= 0 && xd < g.n) cbr[xd] = cb[n1] + 2.f * hv[n1] * p_b / c;
-            const float acx = fa[n1];
+            const bool xin = yin && xd >= 0 && xd < g.n;
+            float v0, v1, c, acx, cbo, h;
+            if constexpr (STAGE) {
+                v0 = Sx[r * N + x];
+                v1 = Sy[r * N + x];
+                c = Sc[r * N + x];
+                acx = Sa[x];
+                h = Sh[r * N + x];
+                cbo = xin ? (cb_staged ? Sb[(yd - d0) * g.n + xd] : cbr[xd]) : 0.f;
+            } else {
+                v0 = s0[n1];
+                v1 = s1[n1];
+                c = cc[n1];
+                acx = fa[n1];
+                cbo = cb[n1];
+                h = hv[n1];
+            }
+            const float p_b = PB[r * N + x];
+            const float c2 = c * c;
+            const float vbx = v0 + c2 * p_b;
+            const float vby = v1 + c2 * p_b;
+            if (xin) cbr[xd] = cbo + 2.f * h * p_b / c;
             const float tx = acx * vbx, ty = acy * vby;
             bx[x] = acx * tx;
             by[x] = acy * ty;
@@ -530,25 +691,30 @@ inline void launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t sme
     cudaLaunchKernelEx(&cfg, kern, args...);
 }
 
-template <int N1, int N2, int RR, int CC>
+template <int N1, int N2, int RR, int CC, bool STAGE>
 struct FixedImpl {
     using F = Fft2<N1, N2>;
+    using RS = RowSmem<F, RR>;
     static constexpr size_t smem_col = (F::N + 2 * F::N * CC + 4 * F::ZS * CC) * sizeof(float2);
     static_assert(2 * F::ZS >= F::ZS + F::N1 * F::N2, "product hand-off fits the inverse buffer");
-    static constexpr size_t smem_row = RowSmem<F, RR>::bytes;
+    static_assert(!STAGE || (F::N % 4 == 0 && RR % 2 == 0), "staged row blocks are 16-byte multiples");
+    // staged: velocity 2 arrays, density 3, adjoint density 4 and the dJ/dc rows (n < Ng)
+    static constexpr size_t smem_u = STAGE ? RS::staged(2, 0, 0) : RS::base;
+    static constexpr size_t smem_rho = STAGE ? RS::staged(3, 0, 0) : RS::base;
+    static constexpr size_t smem_adj = STAGE ? RS::staged(4, 1, F::N) : RS::base;
 
     static int configure() {
         cudaError_t e = cudaFuncSetAttribute((const void*)kf_col<N1, N2, CC>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem_col));
         if (e == cudaSuccess)
-            e = cudaFuncSetAttribute((const void*)kf_row_u<N1, N2, RR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     int(smem_row));
+            e = cudaFuncSetAttribute((const void*)kf_row_u<N1, N2, RR, STAGE>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem_u));
         if (e == cudaSuccess)
-            e = cudaFuncSetAttribute((const void*)kf_row_rho<N1, N2, RR>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem_row));
+            e = cudaFuncSetAttribute((const void*)kf_row_rho<N1, N2, RR, STAGE>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem_rho));
         if (e == cudaSuccess)
-            e = cudaFuncSetAttribute((const void*)kf_row_adj_rho<N1, N2, RR>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem_row));
+            e = cudaFuncSetAttribute((const void*)kf_row_adj_rho<N1, N2, RR, STAGE>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem_adj));
         return e == cudaSuccess ? PAT_OK : cuda_fail(e, "cudaFuncSetAttribute(fixed-size kernels)");
     }
     static void col(const Geo& g, cudaStream_t st, float2* A, float2* B, int mode, int op, float scale) {
@@ -558,23 +724,40 @@ struct FixedImpl {
     static void row_u(const Geo& g, cudaStream_t st, float2* A, float2* B, float* ux, float* uy, int kind,
                       int init) {
         dim3 grid((F::N + RR - 1) / RR, g.K);
-        launch_pdl(kf_row_u<N1, N2, RR>, grid, dim3(RR * F::T), smem_row, st, true, g, A, B, ux, uy, kind, init);
+        launch_pdl(kf_row_u<N1, N2, RR, STAGE>, grid, dim3(RR * F::T), smem_u, st, true, g, A, B, ux, uy, kind,
+                   init);
     }
     static void row_rho(const Geo& g, cudaStream_t st, float2* A, const float2* B, float* rx, float* ry,
                         const float* cg, int mode, const float* p0, float* y, int tstep, float* hist, int slot) {
         dim3 grid((F::N + RR - 1) / RR, g.K);
-        launch_pdl(kf_row_rho<N1, N2, RR>, grid, dim3(RR * F::T), smem_row, st, mode == 0, g, A, B, rx, ry, cg, mode, p0, y,
-                   tstep, hist, slot);
+        launch_pdl(kf_row_rho<N1, N2, RR, STAGE>, grid, dim3(RR * F::T), smem_rho, st, mode == 0, g, A, B, rx, ry,
+                   cg, mode, p0, y, tstep, hist, slot);
     }
     static void row_adj_rho(const Geo& g, cudaStream_t st, float2* A2, float2* B2, float* rbx, float* rby,
                             float* cbar, const float* cg, int first, const float* resid, int tstep,
                             const float* hist, int slot) {
         dim3 grid((F::N + RR - 1) / RR, g.K);
-        launch_pdl(kf_row_adj_rho<N1, N2, RR>, grid, dim3(RR * F::T), smem_row, st, true, g, A2, B2, rbx, rby, cbar, cg,
-                   first, resid, tstep, hist, slot);
+        launch_pdl(kf_row_adj_rho<N1, N2, RR, STAGE>, grid, dim3(RR * F::T), smem_adj, st, true, g, A2, B2, rbx,
+                   rby, cbar, cg, first, resid, tstep, hist, slot);
+    }
+    static FixedOps ops() { return FixedOps{F::N, RR, CC, &configure, &col, &row_u, &row_rho, &row_adj_rho}; }
+};
+
+// A variant whose pass kinds come from different tile shapes / factorisations of the same
+// Ng (the half spectra in global memory have one layout): column passes from C, velocity
+// row passes from U, density row passes from R, adjoint density row passes from J.
+template <class C, class U, class R, class J>
+struct MixedImpl {
+    static_assert(C::F::N == U::F::N && C::F::N == R::F::N && C::F::N == J::F::N, "one grid side");
+    static int configure() {
+        int rc = C::configure();
+        if (rc == PAT_OK) rc = U::configure();
+        if (rc == PAT_OK) rc = R::configure();
+        if (rc == PAT_OK) rc = J::configure();
+        return rc;
     }
     static FixedOps ops() {
-        return FixedOps{F::N, RR, CC, &configure, &col, &row_u, &row_rho, &row_adj_rho};
+        return FixedOps{C::F::N, 0, 0, &configure, &C::col, &U::row_u, &R::row_rho, &J::row_adj_rho};
     }
 };
 

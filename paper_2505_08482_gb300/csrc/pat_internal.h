@@ -118,6 +118,7 @@ struct Launch {
 };
 
 int configure_kernels(pat_plan_s* p);
+int check_launch(const char* what);   // PAT_OK or the pending launch error
 int select_variant(pat_plan_s* p, int variant);
 
 // forward

@@ -59,6 +59,11 @@ __global__ void k_axpby(float* __restrict__ out, float a, const float* __restric
         out[i] = a * x[i] + (y ? b * y[i] : 0.f);
 }
 
+__global__ void k_fill(float* __restrict__ y, float v, size_t n) {
+    for (size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += size_t(gridDim.x) * blockDim.x)
+        y[i] = v;
+}
+
 // out[i] = v[i] * s_b or / s_b with s_b = s0 for i < n0 and s1 otherwise
 __global__ void k_blockscale(float* __restrict__ out, const float* __restrict__ v, size_t n, size_t n0, float s0,
                              float s1, int divide) {
@@ -191,6 +196,11 @@ int vscale_dev(cudaStream_t st, float* y, const float* x, size_t n, const double
 int vaxpby(cudaStream_t st, float* out, float a, const float* x, float b, const float* y, size_t n) {
     k_axpby<<<blocks_for(n), 256, 0, st>>>(out, a, x, b, y, n);
     return chk("vaxpby");
+}
+
+int vfill(cudaStream_t st, float* y, float v, size_t n) {
+    k_fill<<<blocks_for(n), 256, 0, st>>>(y, v, n);
+    return chk("vfill");
 }
 
 int vblockscale(cudaStream_t st, float* out, const float* v, size_t n, size_t n0, float s0, float s1, int divide) {

@@ -20,6 +20,7 @@ int vaxpy_dev(cudaStream_t st, float* y, const float* x, size_t n, const double*
               float sign);
 int vscale_dev(cudaStream_t st, float* y, const float* x, size_t n, const double* coef, float sign);
 int vaxpby(cudaStream_t st, float* out, float a, const float* x, float b, const float* y, size_t n);
+int vfill(cudaStream_t st, float* y, float v, size_t n);
 int vblockscale(cudaStream_t st, float* out, const float* v, size_t n, size_t n0, float s0, float s1, int divide);
 int vproject(cudaStream_t st, float* zt, float* xt, const float* z, const float* d, float alpha, size_t n,
              size_t n0, const Box& box);

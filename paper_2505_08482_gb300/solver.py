@@ -193,22 +193,31 @@ class Plan:
         """Capture whole calls into CUDA graphs and replay them (pat_plan_set_graphs)."""
         B.check(B.lib().pat_plan_set_graphs(self._h, int(bool(enable))), "pat_plan_set_graphs")
 
-    def autotune(self, stream=None):
-        """Time every kernel variant on this GPU and keep the fastest; returns ms/step per variant."""
+    def autotune(self, stream=None, gradient=True):
+        """Time every kernel variant on this GPU and keep the fastest (pat_plan_autotune).
+
+        gradient: time whole gradient evaluations on the gradient workspace (else forward
+        steps on the forward workspace).  Returns {variant: ms per evaluation or per step}.
+        """
         nv = self.variants
         ms = (ctypes.c_double * (max(nv, 0) + 1))()
-        ws = self.workspace(B.PAT_WS_FORWARD)
+        kind = B.PAT_WS_GRADIENT if gradient else B.PAT_WS_FORWARD
+        ws = self.workspace(kind)
         with torch.cuda.device(self.device):
-            B.check(B.lib().pat_plan_autotune(self._h, _ptr(ws), self.workspace_bytes(B.PAT_WS_FORWARD), ms,
-                                              _stream(stream)), "pat_plan_autotune")
+            B.check(B.lib().pat_plan_autotune(self._h, _ptr(ws), self.workspace_bytes(kind), ms, _stream(stream)),
+                    "pat_plan_autotune")
         return {v: ms[v + 1] for v in range(-1, max(nv, 0))}
+
+    def status(self, kind: int = B.PAT_WS_GRADIENT, stream=None) -> int:
+        """pat_status of a cached workspace: PAT_STATUS_NONFINITE | PAT_STATUS_WAIT bits (synchronises)."""
+        flag = ctypes.c_int(0)
+        ws = self.workspace(kind)
+        B.check(B.lib().pat_status(self._h, _ptr(ws), ctypes.byref(flag), _stream(stream)), "pat_status")
+        return int(flag.value)
 
     def nonfinite(self, stream=None) -> bool:
         """True if the last objective on the gradient workspace met NaN/Inf (synchronises)."""
-        flag = ctypes.c_int(0)
-        ws = self.workspace(B.PAT_WS_GRADIENT)
-        B.check(B.lib().pat_status(self._h, _ptr(ws), ctypes.byref(flag), _stream(stream)), "pat_status")
-        return bool(flag.value)
+        return bool(self.status(B.PAT_WS_GRADIENT, stream) & B.PAT_STATUS_NONFINITE)
 
 
 @dataclass

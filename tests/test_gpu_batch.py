@@ -28,13 +28,15 @@ def _instances(n, Ks, nt, seed=0):
     return out
 
 
-@pytest.mark.parametrize("n", [40, 64])
-def test_batched_plan_equals_single_plans(n):
+@pytest.mark.parametrize("n,variant", [(40, None), (64, 0), (64, 3)])
+def test_batched_plan_equals_single_plans(n, variant):
     Ks = [1, 3, 2]
     xy = ps.circle_sensors(n, 16, 1e-4)
     gp = grid_params(n, 90)
     inst = _instances(n, Ks, 90)
     bplan = gpu_plan(gp, xy, Ks, ckpt_every=16)
+    if variant is not None:
+        bplan.variant = variant
     c_b = _dev(np.stack([c for c, _ in inst]))
     p0_b = _dev(np.concatenate([p for _, p in inst]))
     yb = bplan.forward(c_b, p0_b)
@@ -47,6 +49,8 @@ def test_batched_plan_equals_single_plans(n):
     for i, (c, p0) in enumerate(inst):
         K = Ks[i]
         plan = gpu_plan(gp, xy, K, ckpt_every=16)
+        if variant is not None:
+            plan.variant = variant
         y = plan.forward(_dev(c), _dev(p0))
         assert torch.equal(y, yb[k0:k0 + K])
         J, gp0, gc = plan.adjoint_grad(c0[i].contiguous(), (0.5 * p0_b[k0:k0 + K]).contiguous(),
@@ -89,9 +93,10 @@ def test_autotune_selects_a_variant_with_identical_physics():
     gp = grid_params(n, 60)
     (c, p0), = _instances(n, [4], 60, seed=2)
     plan = gpu_plan(gp, xy, 4)
-    ms = plan.autotune()
-    assert set(ms) == {-1, 0, 1} and all(v > 0 for v in ms.values())
-    assert plan.variant == min(ms, key=ms.get)
+    for gradient in (False, True):   # forward steps, then whole gradient evaluations
+        ms = plan.autotune(gradient=gradient)
+        assert set(ms) == set(range(-1, plan.variants)) and all(v > 0 for v in ms.values())
+        assert plan.variant == min(ms, key=ms.get)
     y = plan.forward(_dev(c), _dev(p0)).cpu().numpy()
     plan.variant = -1
     assert rel_l2(y, plan.forward(_dev(c), _dev(p0)).cpu().numpy()) <= 1e-5

@@ -130,3 +130,26 @@ def test_nonfinite_flag():
     assert plan.nonfinite()
     plan.adjoint_grad(_dev(c), _dev(p0[:1]), _dev(np.zeros_like(ym)), _dev(np.ones(1)))
     assert not plan.nonfinite()
+
+
+@pytest.mark.parametrize("variant", [-1, 0, 3])
+def test_vjp_with_stale_history_recomputes_last_segment(variant):
+    # Nt - 1 = 2 s: the last segment holds the single level Nt - 1, restored from the
+    # checkpoint taken when the forward sweep reaches it
+    n, nt, s = 64, 33, 16
+    xy = ps.circle_sensors(n, 16, 1e-4)
+    gp = grid_params(n, nt)
+    rng = ps.rng_for(31)
+    c = _dev(ps.ellipse_phantom(n, 3, rng))
+    p0 = _dev(np.stack([ps.vessel_p0(n, rng) for _ in range(2)]))
+    ybar = _dev(rng.standard_normal((2, nt, 16)))
+    plan = gpu_plan(gp, xy, 2, ckpt_every=s)
+    plan.variant = variant
+    plan.forward(c, p0, keep_checkpoints=True)
+    g1 = [t.clone() for t in plan.vjp(c, p0, ybar)]          # history of the last segment kept
+    plan.forward(c, p0, keep_checkpoints=True)
+    plan.forward(c, p0)                                      # forward workspace: history now stale
+    g2 = plan.vjp(c, p0, ybar)                               # last segment recomputed
+    assert torch.equal(g1[0], g2[0]) and torch.equal(g1[1], g2[1])
+    from paper_2505_08482_gb300 import _binding as B
+    assert not plan.status() & B.PAT_STATUS_WAIT            # no bounded wait gave up

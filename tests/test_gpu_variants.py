@@ -1,4 +1,5 @@
-"""Every kernel variant (generic Stockham, fixed-size two-level tiles) against the oracle.
+"""Every kernel variant (generic Stockham, fixed-size two-level tiles with the state in
+registers or staged in shared memory) against the oracle.
 
 Grid sides 108, 144, 180, 200, 240, 300 (domains 64..256 with the automatic
 PML) have compiled two-level FFT passes; each variant must reproduce the
@@ -38,13 +39,14 @@ def test_forward_all_variants(n):
     g = oracle_grid(gp)
     ref = forward(g, c, p0, sensor_matrix(g, xy))
     plan = gpu_plan(gp, xy, 2)
-    assert plan.variants == 2 and plan.variant == 0
+    assert plan.variants >= 3 and plan.variant == 0
     outs = {}
-    for v in (-1, 0, 1):
+    for v in range(-1, plan.variants):
         plan.variant = v
         outs[v] = plan.forward(_dev(c), _dev(p0)).cpu().numpy()
         assert rel_l2(outs[v], ref) <= 1e-4, (v, rel_l2(outs[v], ref))
-    assert rel_l2(outs[0], outs[-1]) <= 1e-5 and rel_l2(outs[1], outs[-1]) <= 1e-5
+    for v in range(plan.variants):
+        assert rel_l2(outs[v], outs[-1]) <= 1e-5, v
 
 
 @pytest.mark.parametrize("n", [64, 160, 256])
@@ -63,7 +65,7 @@ def test_gradient_all_variants(n):
     c0 = np.full((n, n), 1520.0)
     J, gp0, gc = adjoint_grad(g, c0, 0.5 * p0, S, ym, wt)
     plan = gpu_plan(gp, xy, 2, ckpt_every=16)
-    for v in (-1, 0, 1):
+    for v in range(-1, plan.variants):
         plan.variant = v
         Jg, a, b = plan.adjoint_grad(_dev(c0), _dev(0.5 * p0), _dev(ym), _dev(wt))
         assert abs(Jg.item() - J) <= 1e-4 * J, v
