@@ -211,6 +211,14 @@ int pat_vjp(pat_plan plan, const float* d_c, const float* d_p0, const float* d_y
  * staged copies (variant 3; the results of that call are then invalid). */
 #define PAT_STATUS_NONFINITE 1
 #define PAT_STATUS_WAIT 2
+
+/* Self-test of the bounded wait behind PAT_STATUS_WAIT: launches one CTA on
+ * the stream whose threads wait for an mbarrier phase that never completes
+ * (nothing arrives, no copy is in flight), give up after timeout_us
+ * microseconds (1..1000000) and OR PAT_STATUS_WAIT into the device int
+ * *d_status.  No fault and no hang: the context stays usable.  PAT_EINVAL
+ * for a NULL pointer or a timeout out of range. */
+int pat_selftest_wait(int* d_status, unsigned timeout_us, void* stream);
 int pat_status(pat_plan plan, const void* d_ws, int* h_flag, void* stream);
 
 /* ---- reconstruction (Sec. 3, Sec. 3.1) ---- */

@@ -87,6 +87,7 @@ SIGNATURES = {
                                  c_void_p, c_void_p, c_size_t, c_void_p]),
     "pat_vjp": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),
     "pat_status": (c_int, [c_void_p, c_void_p, POINTER(c_int), c_void_p]),
+    "pat_selftest_wait": (c_int, [c_void_p, ctypes.c_uint, c_void_p]),
     "pat_reconstruct": (c_int, [POINTER(PatReconCfg), c_void_p, c_void_p, c_void_p, c_void_p, POINTER(PatReport),
                                 c_void_p]),
     "pat_reconstruct_batched": (c_int, [POINTER(PatReconCfg), c_int, POINTER(PatInstance), c_void_p]),

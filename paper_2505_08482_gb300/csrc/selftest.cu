@@ -1,0 +1,35 @@
+// Self-test of the bounded mbarrier wait used by the staged row passes: one CTA
+// waits for a phase that nothing completes (no arrival, no copy in flight), gives
+// up after the given time and reports it in the status word, as a staged pass
+// whose copies never land would.
+#include <cuda_runtime.h>
+
+#include "kfixed.cuh"
+#include "pat_internal.h"
+
+namespace pat {
+namespace {
+
+__global__ void k_selftest_wait(int* status, unsigned long long limit_ns) {
+    __shared__ uint64_t mb;
+    if (threadIdx.x == 0) mbar_init(&mb, 1);   // one arrival expected, none comes
+    __syncthreads();
+    mbar_wait(&mb, 0, status, limit_ns);
+}
+
+}  // namespace
+}  // namespace pat
+
+using namespace pat;
+
+extern "C" int pat_selftest_wait(int* d_status, unsigned timeout_us, void* stream) {
+    if (!d_status) { set_error("pat_selftest_wait: null status"); return PAT_EINVAL; }
+    if (timeout_us == 0 || timeout_us > 1000000u) {
+        set_error("pat_selftest_wait: timeout_us must be in 1..1000000");
+        return PAT_EINVAL;
+    }
+    count_launch();
+    k_selftest_wait<<<1, 64, 0, static_cast<cudaStream_t>(stream)>>>(d_status, 1000ull * timeout_us);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? PAT_OK : cuda_fail(e, "k_selftest_wait");
+}

@@ -153,3 +153,20 @@ def test_vjp_with_stale_history_recomputes_last_segment(variant):
     assert torch.equal(g1[0], g2[0]) and torch.equal(g1[1], g2[1])
     from paper_2505_08482_gb300 import _binding as B
     assert not plan.status() & B.PAT_STATUS_WAIT            # no bounded wait gave up
+
+
+def test_bounded_wait_gives_up_and_reports():
+    # a wait that nothing completes ends after its limit, sets PAT_STATUS_WAIT, and the
+    # context stays usable for the solver afterwards
+    from paper_2505_08482_gb300 import _binding as B
+    st = torch.zeros((), dtype=torch.int32, device="cuda")
+    s = torch.cuda.current_stream()
+    B.check(B.lib().pat_selftest_wait(st.data_ptr(), 2000, s.cuda_stream), "pat_selftest_wait")
+    torch.cuda.synchronize()
+    assert st.item() & B.PAT_STATUS_WAIT
+    with pytest.raises(B.PatError):
+        B.check(B.lib().pat_selftest_wait(st.data_ptr(), 0, s.cuda_stream), "pat_selftest_wait")
+    c, p0, xy = small_case(K=1, nt=40)
+    plan = gpu_plan(grid_params(40, 40), xy, 1)
+    y = plan.forward(_dev(c), _dev(p0))
+    assert torch.isfinite(y).all()
