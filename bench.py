@@ -234,8 +234,8 @@ def run_reference(args, rank):
 
 def cfg_dict(args):
     return {"workload": f"{WL['workload']}: 256x256 domain (Ng 300, PML 22), K=8 vessel p0 sets, "
-                        f"M=512 circle sensors, Nt=1800, s={args.ckpt}, 6 c inclusions",
-            "global_batch": WL["K"] * args.gpus, "n": WL["n"], "K": WL["K"], "M": WL["M"], "nt": WL["nt"],
+                        f"M=512 circle sensors, Nt={args.nt}, s={args.ckpt}, 6 c inclusions",
+            "global_batch": WL["K"] * args.gpus, "n": WL["n"], "K": WL["K"], "M": WL["M"], "nt": args.nt,
             "ckpt_every": args.ckpt, "parallelism": f"replicas x{args.gpus}",
             "l2": "256 MiB buffer written between timed steps (working set of one step is L2-resident)"}
 
