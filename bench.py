@@ -90,6 +90,9 @@ def parse():
     ap.add_argument("--batch-instances", type=int, default=64)
     ap.add_argument("--batch-iters", type=int, default=2)
     ap.add_argument("--batch-plain", type=int, default=64, help="instances also solved one by one")
+    ap.add_argument("--roofline-k", type=int, default=0,
+                    help="per-pass bandwidth of forward steps with this many data sets on the headline grid "
+                         "(working set beyond L2 for K >= 64); uses --nt and --variant")
     ap.add_argument("--warmstart", action="store_true",
                     help="learned warm start: train the U-Net on solver-generated pairs, compare with the plain start")
     ap.add_argument("--ws-train", type=int, default=20000)
@@ -543,6 +546,75 @@ def run_batch(args):
     print(json.dumps(line), flush=True)
 
 
+def run_roofline_k(args):
+    """Per-pass achieved bandwidth of forward sweeps on the 300^2 grid with K data sets.
+
+    At K = 8 the state and spectra of a step (about 30 MB) stay in L2 and the passes are
+    latency-bound; with K = 64 they take about 140 MB, more than L2, so each pass streams its
+    fields through HBM.  The K data sets are the headline's eight vessel sets repeated.
+    """
+    import numpy as np
+    import torch
+
+    import paper_2505_08482_gb300 as pkg
+    from paper_2505_08482_gb300 import _binding as B
+    from paper_2505_08482_gb300.solver import GridSpec, Plan
+
+    pkg.build()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(0)
+    L = B.lib()
+    w, _ = inputs(0)
+    n, K, nt = WL["n"], args.roofline_k, args.nt
+    P = pml_auto(n)
+    dt = WL["cfl"] * WL["dx"] / WL["c_hi"]
+    gs = GridSpec(n=n, pml=P, dx=WL["dx"], dt=dt, nt=nt, c_ref=WL["c_hi"], pml_alpha=WL["pml_alpha"],
+                  c_bg=WL["c_bg"])
+    ng = gs.ng
+    plan = Plan(gs, w.sensors, K, ckpt_every=args.ckpt, device=dev)
+    if args.variant is None:
+        plan.autotune(gradient=False)
+    else:
+        plan.variant = args.variant
+    f32 = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float32, device=dev)
+    reps = -(-K // w.p0_true.shape[0])
+    c, p0 = f32(w.c_true), f32(np.concatenate([w.p0_true] * reps)[:K])
+    y = torch.empty((K, nt, WL["M"]), dtype=torch.float32, device=dev)
+    stream = torch.cuda.Stream(device=dev)
+    torch.cuda.set_stream(stream)
+    for _ in range(max(args.warmup, 1)):
+        plan.forward(c, p0, y=y, stream=stream)
+    torch.cuda.synchronize()
+    peak, peak_kind = measured_peaks()
+    passes = {}
+    for cls in (3, 2, 4, 1):     # the four passes of a forward step
+        B.check(L.pat_timing_enable(cls, nt + 8, 1), "pat_timing_enable")
+        plan.forward(c, p0, y=y, stream=stream)
+        tot, cnt = ctypes_read(L)
+        B.check(L.pat_timing_enable(0, 0, 1), "pat_timing_enable")
+        bpl = bytes_per_cell(cls, ng, n, ckpt_hist=False) * ng * ng * K
+        us = tot * 1000.0 / max(cnt, 1)
+        passes[B.KERNEL_CLASSES[cls]] = {"launches": cnt, "avg_launch_us": round(us, 2),
+                                         "algorithmic_bytes_per_launch": bpl,
+                                         "achieved_gbs": round(bpl / (us * 1e-6) / 1e9, 1),
+                                         "frac": round(bpl / (us * 1e-6) / 1e9 / peak, 3)}
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        plan.forward(c, p0, y=y, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    fwd_s = e0.elapsed_time(e1) / 1000.0 / args.steps
+    print(json.dumps({"metric": f"per-pass achieved algorithmic HBM GB/s, forward sweep at K={K}",
+                      "unit": "GB/s", "n_gpus": 1, "dtype": "f32", "data": "synthetic",
+                      "config": {"workload": f"vessels256 grid (Ng {ng}) with K={K} data sets, M={WL['M']}, "
+                                             f"Nt={nt}", "K": K, "nt": nt},
+                      "variant": plan.variant, "peak": peak, "peak_kind": f"{peak_kind} hbm_gbs",
+                      "passes": passes, "forward_ms": fwd_s * 1000.0,
+                      "forward_gcell_steps_per_s": ng * ng * K * (nt - 1) / fwd_s / 1e9,
+                      "kernel_source_hash": kernel_source_hash()}), flush=True)
+
+
 def run_warmstart(args):
     """Learned warm start (128x128, K=4): iterations and time to E_c <= 2 % with and without it."""
     import numpy as np
@@ -634,6 +706,9 @@ def main():
         return
     if args.warmstart:
         run_warmstart(args)
+        return
+    if args.roofline_k:
+        run_roofline_k(args)
         return
     if world > 1:
         import torch
