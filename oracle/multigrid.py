@@ -21,6 +21,7 @@ import numpy as np
 from .adjoint import adjoint_grad, objective
 from .grid import make_grid
 from .lbfgs import projected_lbfgs
+from .prior import OUPrior, prior_value_grad
 from .sensors import sensor_matrix
 
 
@@ -63,12 +64,15 @@ def prolong(f, n_dst: int):
 
 def reconstruct(levels, L, T, sensors_xy, y_meas, dt_data, w, c_init, c_bounds,
                 p0_lower=0.0, cfl=0.3, mem=20, iters=20, rtol=1e-4, alpha0=0.1,
-                sigma_p0=0.25, c_bg=1500.0, min_pml=20, callback=None):
+                sigma_p0=0.25, c_bg=1500.0, min_pml=20, callback=None, prior=None):
     """Joint reconstruction of p0[K] and c over the multigrid levels.
 
     ``levels``: domain sides N_l (coarse to fine); ``L``: domain side (m);
     ``y_meas``: data [K][Nt][M] at times n * dt_data; ``w``: weights [K];
     ``c_bounds``: (L_c, U_c), also the reference speed c_ref = U_c.
+    ``prior``: None (data term only) or a dict with tau (m), eta_c, sigma_c,
+    eta_p0, sigma_p0: the Ornstein-Uhlenbeck prior terms of Eq.
+    (Minimised_functional) on each level's grid (oracle/prior.py).
     Returns (p0[K][N][N], c[N][N], history) on the finest level.
     """
     Lc, Uc = c_bounds
@@ -94,16 +98,26 @@ def reconstruct(levels, L, T, sensors_xy, y_meas, dt_data, w, c_init, c_bounds,
         upper = np.concatenate([np.full(K * npx, np.inf), np.full(npx, Uc)])
         scale = np.concatenate([np.full(K * npx, sigma_p0), np.full(npx, (Uc - Lc) / 4.0)])
 
+        pr = OUPrior((nl, nl), dx, prior["tau"]) if prior else None
+
         def unpack(x):
             return x[:K * npx].reshape(K, nl, nl), x[K * npx:].reshape(nl, nl)
 
+        def prior_part(pp, cc):
+            return prior_value_grad(pr, pp, cc, prior["eta_p0"], prior["sigma_p0"], prior["eta_c"],
+                                    prior["sigma_c"])
+
         def fun(x):
             pp, cc = unpack(x)
-            return objective(g, cc, pp, S, yl, w)[0]
+            J = objective(g, cc, pp, S, yl, w)[0]
+            return J + (prior_part(pp, cc)[0] if pr else 0.0)
 
         def fun_grad(x):
             pp, cc = unpack(x)
             J, gp, gc = adjoint_grad(g, cc, pp, S, yl, w)
+            if pr:
+                Jp, gpp, gcp = prior_part(pp, cc)
+                J, gp, gc = J + Jp, gp + gpp, gc + gcp
             return J, np.concatenate([gp.ravel(), gc.ravel()])
 
         res = projected_lbfgs(fun, fun_grad, x0, lower, upper, scale, mem=mem, max_iter=iters,
