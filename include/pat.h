@@ -221,6 +221,47 @@ int pat_vjp(pat_plan plan, const float* d_c, const float* d_p0, const float* d_y
 int pat_selftest_wait(int* d_status, unsigned timeout_us, void* stream);
 int pat_status(pat_plan plan, const void* d_ws, int* h_flag, void* stream);
 
+/* ---- Ornstein-Uhlenbeck prior (Eq. Minimised_functional, Sec. 4.1.2) ---- */
+
+/* The regularising terms of the objective: for a field z on an n x n pixel
+ * grid of spacing dx (m), P(z) = 1/2 (z - eta)^T Xi^{-1} (z - eta) / sigma^2
+ * with the unit covariance Xi_ij = exp(-|r_i - r_j| / tau), r_i the pixel
+ * centres, tau the characteristic length (m); dP/dz = Xi^{-1}(z - eta)/sigma^2.
+ * Xi v is computed exactly as a linear convolution through a zero-padded FFT
+ * of side M >= 2n - 1; Xi^{-1} b by preconditioned conjugate gradients (the
+ * padded circulant's inverse as preconditioner), batched over fields, FP32
+ * vectors with FP64 dot products.  Fields are device arrays [nf][n][n]
+ * float, nf <= max_fields.  All calls run on `stream`; pat_prior_solve and
+ * pat_prior_eval synchronise it (convergence checks).  A prior object owns
+ * its device buffers (about 5 max_fields n^2 floats plus the transforms);
+ * calls on one object must not overlap. */
+typedef struct pat_prior_s* pat_prior;
+
+/* Create for the current device: 2 <= n <= 512, dx > 0, tau > 0,
+ * 1 <= max_fields <= 1024 (PAT_EINVAL otherwise).  Builds the spectrum of
+ * the embedding on the host in FP64 (O(M^3), about 0.3 s at n = 256). */
+int pat_prior_create(int n, double dx, double tau, int max_fields, pat_prior* out);
+int pat_prior_destroy(pat_prior prior);
+
+/* d_out = Xi d_v for nf fields. */
+int pat_prior_xi(pat_prior prior, const float* d_v, float* d_out, int nf, void* stream);
+
+/* Solve Xi d_z = d_b for nf fields to a relative residual |r| <= tol |b|
+ * per field, at most maxit iterations; warm != 0 starts from d_z's contents,
+ * else from zero.  *h_iters (may be NULL) receives the iterations taken. */
+int pat_prior_solve(pat_prior prior, const float* d_b, float* d_z, int nf, double tol, int maxit, int warm,
+                    int* h_iters, void* stream);
+
+/* Prior terms of nf fields d_x with means h_eta[nf] and standard deviations
+ * h_sigma[nf] (host arrays): d_z [nf][n][n] receives Xi^{-1}(x - eta) (warm:
+ * start from its contents); *d_J (device double, may be NULL) is increased by
+ * sum_f P(x_f); d_grad (may be NULL) is increased by gscale_f dP/dx_f
+ * (h_gscale may be NULL: 1).  tol, maxit, warm, h_iters as in
+ * pat_prior_solve. */
+int pat_prior_eval(pat_prior prior, const float* d_x, int nf, const double* h_eta, const double* h_sigma,
+                   const double* h_gscale, float* d_z, float* d_grad, double* d_J, double tol, int maxit,
+                   int warm, int* h_iters, void* stream);
+
 /* ---- reconstruction (Sec. 3, Sec. 3.1) ---- */
 
 /* Configuration of pat_reconstruct.  levels[nlevels]: domain sides N_l,
@@ -259,6 +300,13 @@ typedef struct {
     double c1;
     double sigma_p0;
     int autotune;   /* nonzero: run pat_plan_autotune on every level's plan */
+    /* Ornstein-Uhlenbeck prior terms of Eq. Minimised_functional (Sec. 4.1.2):
+     * prior_tau > 0 (m) adds, on every level's grid, 1/2 |L_c (c - eta_c)|^2
+     * and 1/2 |L_p0 (p0_k - eta_p0)|^2 for every k to J (see pat_prior_eval;
+     * prior means and standard deviations below, sigmas > 0); 0: data term only. */
+    double prior_tau;
+    double prior_eta_c, prior_sigma_c;
+    double prior_eta_p0, prior_sigma_p0;
 } pat_recon_cfg;
 
 /* One row per L-BFGS iteration. */

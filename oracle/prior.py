@@ -30,9 +30,10 @@ def pixel_points(shape, dx: float):
     return np.stack([xx.ravel(), yy.ravel()], axis=1)
 
 
-def unit_covariance(points, tau: float):
-    """Xi_ij = exp(-||r_i - r_j|| / tau) (Sec. 4.1.2)."""
-    d = np.sqrt(((points[:, None, :] - points[None, :, :]) ** 2).sum(-1))
+def unit_covariance(points, tau: float, rows=None):
+    """Xi_ij = exp(-||r_i - r_j|| / tau) (Sec. 4.1.2); rows: only those rows i (index array)."""
+    a = points if rows is None else points[np.asarray(rows)]
+    d = np.sqrt(((a[:, None, :] - points[None, :, :]) ** 2).sum(-1))
     return np.exp(-d / tau)
 
 

@@ -47,7 +47,8 @@ class PatReconCfg(ctypes.Structure):
                 ("c_bg", c_double), ("rho0", c_double), ("pml_alpha", c_double), ("min_pml", c_int),
                 ("mem", c_int), ("iters", c_int), ("max_halvings", c_int), ("ckpt_every", c_int),
                 ("rtol", c_double), ("alpha0", c_double), ("c1", c_double), ("sigma_p0", c_double),
-                ("autotune", c_int)]
+                ("autotune", c_int), ("prior_tau", c_double), ("prior_eta_c", c_double), ("prior_sigma_c", c_double),
+                ("prior_eta_p0", c_double), ("prior_sigma_p0", c_double)]
 
 
 class PatInstance(ctypes.Structure):
@@ -88,6 +89,13 @@ SIGNATURES = {
     "pat_vjp": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),
     "pat_status": (c_int, [c_void_p, c_void_p, POINTER(c_int), c_void_p]),
     "pat_selftest_wait": (c_int, [c_void_p, ctypes.c_uint, c_void_p]),
+    "pat_prior_create": (c_int, [c_int, c_double, c_double, c_int, POINTER(c_void_p)]),
+    "pat_prior_destroy": (c_int, [c_void_p]),
+    "pat_prior_xi": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_void_p]),
+    "pat_prior_solve": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_double, c_int, c_int, POINTER(c_int),
+                                c_void_p]),
+    "pat_prior_eval": (c_int, [c_void_p, c_void_p, c_int, POINTER(c_double), POINTER(c_double), POINTER(c_double),
+                               c_void_p, c_void_p, c_void_p, c_double, c_int, c_int, POINTER(c_int), c_void_p]),
     "pat_reconstruct": (c_int, [POINTER(PatReconCfg), c_void_p, c_void_p, c_void_p, c_void_p, POINTER(PatReport),
                                 c_void_p]),
     "pat_reconstruct_batched": (c_int, [POINTER(PatReconCfg), c_int, POINTER(PatInstance), c_void_p]),

@@ -118,6 +118,7 @@ struct Launch {
 };
 
 int configure_kernels(pat_plan_s* p);
+bool radix_schedule(int n, FftDesc* fd);   // radix 4/5/3/2 schedule of a 5-smooth length
 int check_launch(const char* what);   // PAT_OK or the pending launch error
 int select_variant(pat_plan_s* p, int variant);
 

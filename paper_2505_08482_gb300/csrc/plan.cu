@@ -37,7 +37,7 @@ static bool smooth235(int n) {
 static bool grid_ok(int ng) { return ng >= 4 && ng <= 1024 && ng % 2 == 0 && smooth235(ng); }
 
 // Radix schedule: as many radix-4 stages as possible, then 5, 3, 2.
-static bool radix_schedule(int n, FftDesc* fd) {
+bool radix_schedule(int n, FftDesc* fd) {
     fd->n = n;
     fd->nrad = 0;
     int r = n;

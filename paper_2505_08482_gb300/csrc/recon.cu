@@ -51,6 +51,8 @@ struct Inst {
     size_t V, n0;               // vector length, length of the p0 block
     float *x, *z, *g, *d, *xt, *zt, *gt, *q, *psi;
     float* ct = nullptr;        // true c resampled to the level (E_c tracking), or null
+    float* zp = nullptr;        // Xi^{-1} (x - eta) of the last prior evaluation (its PCG warm start)
+    bool zp_warm = false;
     std::vector<float*> S, Y;   // ring of curvature pairs
     double* lam;                // [mem] device
     double* rho;                // [mem] device
@@ -74,6 +76,7 @@ public:
         : cfg(c), ni(ninst), ins(in), st(st) {}
     ~Batch() {
         for (void* v : allocs) cudaFreeAsync(v, st);
+        if (prior) pat_prior_destroy(prior);
     }
     int run();
 
@@ -92,6 +95,7 @@ private:
     std::vector<double> hJ;
     // batched plan buffers of the current level
     pat_plan plan = nullptr;
+    pat_prior prior = nullptr;      // prior terms on the current level (null: data term only)
     void* ws = nullptr;
     size_t wsb = 0;
     float *bp0 = nullptr, *bc = nullptr, *bgp0 = nullptr, *bgc = nullptr, *bym = nullptr, *bw = nullptr;
@@ -150,6 +154,20 @@ int Batch::evaluate(bool grad, bool trial) {
         }
     } else {
         RC(objective(plan, bc, bp0, bym, bw, dJ, ws, wsb, st));
+    }
+    if (prior) {   // prior terms of Eq. Minimised_functional: into J and the block-scaled gradient
+        const double sp = cfg.sigma_p0, scs = (cfg.c_hi - cfg.c_lo) / 4.0;
+        for (int i = 0; i < ni; ++i) {
+            Inst& s = I[i];
+            std::vector<double> eta(s.K + 1, cfg.prior_eta_p0), sig(s.K + 1, cfg.prior_sigma_p0), gs(s.K + 1, sp);
+            eta[s.K] = cfg.prior_eta_c;
+            sig[s.K] = cfg.prior_sigma_c;
+            gs[s.K] = scs;
+            float* gdst = grad ? (trial ? s.gt : s.g) : nullptr;
+            RC(pat_prior_eval(prior, trial ? s.xt : s.x, s.K + 1, eta.data(), sig.data(), gs.data(), s.zp, gdst,
+                              dJ + i, 1e-5, 500, s.zp_warm ? 1 : 0, nullptr, st));
+            s.zp_warm = true;
+        }
     }
     PAT_CUDA(cudaMemcpyAsync(hJ.data(), dJ, ni * sizeof(double), cudaMemcpyDeviceToHost, st));
     PAT_CUDA(cudaStreamSynchronize(st));
@@ -213,6 +231,13 @@ int Batch::level(int li, const float* const* xprev, int nprev) {
     wsb = pat_workspace_bytes(plan, PAT_WS_GRADIENT);
     RC(alloc(reinterpret_cast<char**>(&ws), wsb));
     if (cfg.autotune) RC(pat_plan_autotune(plan, ws, wsb, nullptr, st));
+    if (prior) pat_prior_destroy(prior);
+    prior = nullptr;
+    if (cfg.prior_tau > 0) {
+        int kmax = 0;
+        for (int i = 0; i < ni; ++i) kmax = std::max(kmax, ins[i].K);
+        RC(pat_prior_create(N, g.dx, cfg.prior_tau, kmax + 1, &prior));
+    }
     if (st) RC(pat_plan_set_graphs(plan, 1));   // one graph per evaluation kind on this level
     const size_t nn = size_t(N) * N;
     RC(alloc(&bp0, Ktot * nn));
@@ -245,6 +270,7 @@ int Batch::level(int li, const float* const* xprev, int nprev) {
         }
         RC(alloc(&s.lam, memsz));
         RC(alloc(&s.rho, memsz));
+        if (prior) RC(alloc(&s.zp, s.V));
         // x0 = resample of the previous level (or of the initial guess); z = P(x0 / sigma)
         RC(vresample(st, xprev[i], s.xt, s.K + 1, nprev, N));
         RC(vblockscale(st, s.zt, s.xt, s.V, s.n0, float(sp), float(sc_c), 1));
@@ -477,7 +503,8 @@ int check_cfg(const pat_recon_cfg* cfg) {
     if (!cfg || cfg->nlevels < 1 || !cfg->levels || cfg->m < 1 || !cfg->h_sensor_xy || cfg->nt_data < 1 ||
         !(cfg->dt_data > 0) || !(cfg->L > 0) || !(cfg->cfl > 0) || !(cfg->c_hi > cfg->c_lo) || cfg->mem < 0 ||
         cfg->iters < 0 || cfg->max_halvings < 0 || cfg->ckpt_every < 1 || !(cfg->sigma_p0 > 0) ||
-        !(cfg->alpha0 > 0)) {
+        !(cfg->alpha0 > 0) || cfg->prior_tau < 0 ||
+        (cfg->prior_tau > 0 && !(cfg->prior_sigma_c > 0 && cfg->prior_sigma_p0 > 0))) {
         set_error("pat_reconstruct: invalid configuration");
         return PAT_EINVAL;
     }

@@ -220,6 +220,75 @@ class Plan:
         return bool(self.status(B.PAT_WS_GRADIENT, stream) & B.PAT_STATUS_NONFINITE)
 
 
+
+class Prior:
+    """Ornstein-Uhlenbeck prior terms on an n x n grid (wraps pat_prior; Sec. 4.1.2).
+
+    ``xi(v)``: Xi v; ``solve(b)``: Xi^{-1} b; ``eval(x, eta, sigma)``: the prior
+    value sum_f 1/2 (x_f - eta_f)^T Xi^{-1} (x_f - eta_f) / sigma_f^2 and its
+    gradient.  Fields are float32 CUDA tensors [nf][n][n].
+    """
+
+    def __init__(self, n: int, dx: float, tau: float, max_fields: int, device=None):
+        self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        self.n, self.max_fields = int(n), int(max_fields)
+        h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            B.check(B.lib().pat_prior_create(self.n, float(dx), float(tau), self.max_fields, ctypes.byref(h)),
+                    "pat_prior_create")
+        self._h = h
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h:
+            try:
+                B.lib().pat_prior_destroy(h)
+            except Exception:
+                pass
+            self._h = None
+
+    def _shape(self, t, name):
+        nf = int(t.shape[0])
+        _f32(t, (nf, self.n, self.n), name, self.device)
+        return nf
+
+    def xi(self, v, stream=None):
+        nf = self._shape(v, "v")
+        out = torch.empty_like(v)
+        with torch.cuda.device(self.device):
+            B.check(B.lib().pat_prior_xi(self._h, _ptr(v), _ptr(out), nf, _stream(stream)), "pat_prior_xi")
+        return out
+
+    def solve(self, b, z=None, tol=1e-6, maxit=500, stream=None):
+        """(Xi^{-1} b, iterations); z: warm start (overwritten with the solution)."""
+        nf = self._shape(b, "b")
+        warm = z is not None
+        if z is None:
+            z = torch.empty_like(b)
+        it = ctypes.c_int(0)
+        with torch.cuda.device(self.device):
+            B.check(B.lib().pat_prior_solve(self._h, _ptr(b), _ptr(z), nf, float(tol), int(maxit), int(warm),
+                                            ctypes.byref(it), _stream(stream)), "pat_prior_solve")
+        return z, it.value
+
+    def eval(self, x, eta, sigma, gscale=None, z=None, grad=None, tol=1e-6, maxit=500, stream=None):
+        """(value, gradient added into ``grad`` (new zeros if None), z, iterations)."""
+        nf = self._shape(x, "x")
+        arr = lambda v: (ctypes.c_double * nf)(*[float(a) for a in v])
+        warm = z is not None
+        if z is None:
+            z = torch.empty_like(x)
+        if grad is None:
+            grad = torch.zeros_like(x)
+        J = torch.zeros((), dtype=torch.float64, device=self.device)
+        it = ctypes.c_int(0)
+        with torch.cuda.device(self.device):
+            B.check(B.lib().pat_prior_eval(self._h, _ptr(x), nf, arr(eta), arr(sigma),
+                                           arr(gscale) if gscale is not None else None, _ptr(z), _ptr(grad),
+                                           _ptr(J), float(tol), int(maxit), int(warm), ctypes.byref(it),
+                                           _stream(stream)), "pat_prior_eval")
+        return float(J.item()), grad, z, it.value
+
 @dataclass
 class ReconConfig:
     """Parameters of pat_reconstruct (see include/pat.h)."""
@@ -246,6 +315,12 @@ class ReconConfig:
     c1: float = 1e-4
     sigma_p0: float = 0.25
     autotune: bool = False
+    # Ornstein-Uhlenbeck prior (Sec. 4.1.2): tau > 0 enables it
+    prior_tau: float = 0.0
+    prior_eta_c: float = 0.0
+    prior_sigma_c: float = 0.0
+    prior_eta_p0: float = 0.0
+    prior_sigma_p0: float = 0.0
 
 
 def _cfg_struct(cfg: ReconConfig, K: int, xy):
@@ -254,7 +329,8 @@ def _cfg_struct(cfg: ReconConfig, K: int, xy):
                           xy.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), K, cfg.cfl, cfg.c_lo, cfg.c_hi,
                           cfg.p0_lo, cfg.c_bg, cfg.rho0, cfg.pml_alpha, cfg.min_pml, cfg.mem, cfg.iters,
                           cfg.max_halvings, cfg.ckpt_every, cfg.rtol, cfg.alpha0, cfg.c1, cfg.sigma_p0,
-                          int(bool(cfg.autotune)))
+                          int(bool(cfg.autotune)), cfg.prior_tau, cfg.prior_eta_c, cfg.prior_sigma_c,
+                          cfg.prior_eta_p0, cfg.prior_sigma_p0)
     return c_cfg, lv
 
 
