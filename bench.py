@@ -93,6 +93,10 @@ def parse():
     ap.add_argument("--roofline-k", type=int, default=0,
                     help="per-pass bandwidth of forward steps with this many data sets on the headline grid "
                          "(working set beyond L2 for K >= 64); uses --nt and --variant")
+    ap.add_argument("--table2", action="store_true",
+                    help="simple-phantom experiment of Sec. 4.1: data on a fine grid (no inverse crime), joint "
+                         "reconstruction with K=4 data sets against K=1 over four multigrid levels")
+    ap.add_argument("--t2-iters", type=int, default=30, help="L-BFGS iterations per level in --table2")
     ap.add_argument("--warmstart", action="store_true",
                     help="learned warm start: train the U-Net on solver-generated pairs, compare with the plain start")
     ap.add_argument("--ws-train", type=int, default=20000)
@@ -615,6 +619,74 @@ def run_roofline_k(args):
                       "kernel_source_hash": kernel_source_hash()}), flush=True)
 
 
+def run_table2(args):
+    """Simple-phantom experiment (Sec. 4.1, Table 2 trend) on the paper's geometry.
+
+    Data: 334 x 334 grid of 63.7 um over the 20 mm target plus its sensor layer, 236 sensors
+    0.2 mm outside the target, dt = 12.1 ns (smaller if the CFL number would exceed 0.3),
+    1747 samples over the same duration, 1 % noise.  Reconstruction on four coarser levels
+    (sides 40, 58, 94, 136: the even sides nearest to the Table 1 pixel sizes) with the
+    Ornstein-Uhlenbeck prior (tau = 1.5 mm, means and deviations as in Sec. 4.1.2), once with
+    all four data sets and once with p0_1 alone; E_c and E_p0^1 on the finest level.
+    """
+    import numpy as np
+    import torch
+
+    import pat_synth as ps
+    import paper_2505_08482_gb300 as pkg
+    from paper_2505_08482_gb300.solver import GridSpec, Plan, ReconConfig, reconstruct
+
+    pkg.build()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(0)
+    L, n_d = ps.SIMPLE_L, 334
+    dx_d = L / n_d
+    T = 1746 * 12.1e-9
+    levels = (40, 58, 94, 136)
+    nf = levels[-1]
+    xy = ps.square_sensors()
+    f32 = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float32, device=dev)
+    err = lambda a, b: float(100.0 * np.linalg.norm(a - b) / np.linalg.norm(a))
+    paper = {"circles": (2.0, 3.2, 17.0, 24.9), "water": (2.1, 3.5, None, None), "bone": (12.0, 14.5, None, None)}
+    out = {}
+    t_all = time.perf_counter()
+    for kind in ("circles", "water", "bone"):
+        U = 3000.0 if kind == "bone" else 1800.0
+        dt_d = min(12.1e-9, 0.3 * dx_d / U)
+        nt_d = int(round(T / dt_d)) + 1
+        c_d, p0_d = ps.simple_phantom_c(kind, n_d), ps.simple_phantom_p0(n_d, 4)
+        gs = GridSpec(n=n_d, pml=pml_auto(n_d), dx=dx_d, dt=dt_d, nt=nt_d, c_ref=U, c_bg=1430.0)
+        plan = Plan(gs, xy, 4, device=dev)
+        y = ps.add_noise(plan.forward(f32(c_d), f32(p0_d)).cpu().numpy(), ps.rng_for(300))
+        wts = ps.noise_weights(y)
+        del plan
+        c_t, p0_t = ps.simple_phantom_c(kind, nf), ps.simple_phantom_p0(nf, 4)
+        eta_c = 1482.0 if kind == "bone" else 0.5 * (1430.0 + 1580.0)
+        sig_c = 0.25 * (c_t.max() - c_t.min())
+        row = {"U_c": U, "data_grid": f"{n_d}^2, dx {dx_d * 1e6:.1f} um, dt {dt_d * 1e9:.2f} ns, Nt {nt_d}"}
+        for K in (4, 1):
+            cfg = ReconConfig(levels=levels, L=L, dt_data=dt_d, nt_data=nt_d, sensors_xy=xy, K=K, cfl=0.3,
+                              c_lo=1300.0, c_hi=U, p0_lo=0.0, c_bg=1430.0, mem=20, iters=args.t2_iters, rtol=1e-5,
+                              sigma_p0=2.5, prior_tau=1.5e-3, prior_eta_c=eta_c, prior_sigma_c=sig_c,
+                              prior_eta_p0=5.0, prior_sigma_p0=2.5)
+            t0 = time.perf_counter()
+            c_r, p0_r, rows, status, ms = reconstruct(cfg, f32(y[:K]), f32(wts[:K]), f32(np.full((nf, nf), eta_c)))
+            wall = time.perf_counter() - t0
+            c_r, p0_r = c_r.cpu().numpy(), p0_r.cpu().numpy()
+            row[f"K{K}"] = {"E_c": err(c_t, c_r), "E_p0_1": err(p0_t[0], p0_r[0]), "iterations": len(rows),
+                            "wall_s": wall, "status": status,
+                            "E_c_initial": err(c_t, np.full_like(c_t, eta_c))}
+        pe = paper[kind]
+        row["paper_table2"] = {"E_c_K4": pe[0], "E_c_K1": pe[1], "E_p0_1_K4": pe[2], "E_p0_1_K1": pe[3]}
+        out[kind] = row
+    print(json.dumps({"metric": "E_c and E_p0^1 (%) of the joint reconstruction, K=4 data sets vs K=1",
+                      "unit": "%", "n_gpus": 1, "dtype": "f32", "data": "synthetic",
+                      "config": {"workload": "simple phantoms of Sec. 4.1 on the paper's 236-sensor square, data "
+                                             "on a finer grid than every reconstruction level, levels "
+                                             f"{levels}, {args.t2_iters} iterations per level, OU prior"},
+                      "results": out, "total_s": time.perf_counter() - t_all}), flush=True)
+
+
 def run_warmstart(args):
     """Learned warm start (128x128, K=4): iterations and time to E_c <= 2 % with and without it."""
     import numpy as np
@@ -709,6 +781,9 @@ def main():
         return
     if args.roofline_k:
         run_roofline_k(args)
+        return
+    if args.table2:
+        run_table2(args)
         return
     if world > 1:
         import torch

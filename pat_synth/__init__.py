@@ -14,8 +14,10 @@ peak-to-peak amplitude of each data set (Sec. 4.1.1), and point sensors.
 """
 from .phantoms import (ellipse_phantom, blob_p0, vessel_p0, circle_sensors,
                        add_noise, noise_weights, workload, Workload, rng_for,
-                       add_noise_torch, warmstart_sample)
+                       add_noise_torch, warmstart_sample, square_sensors, simple_phantom_c,
+                       simple_phantom_p0, SIMPLE_L, SIMPLE_MARGIN, SIMPLE_TARGET)
 
 __all__ = ["ellipse_phantom", "blob_p0", "vessel_p0", "circle_sensors",
            "add_noise", "noise_weights", "workload", "Workload", "rng_for",
-           "add_noise_torch", "warmstart_sample"]
+           "add_noise_torch", "warmstart_sample", "square_sensors", "simple_phantom_c",
+           "simple_phantom_p0", "SIMPLE_L", "SIMPLE_MARGIN", "SIMPLE_TARGET"]

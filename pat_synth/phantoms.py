@@ -222,3 +222,94 @@ def warmstart_sample(n: int, K: int, seed: int):
     c = ellipse_phantom(n, int(rng.integers(2, 9)), rng)
     p0 = np.stack([vessel_p0(n, rng) for _ in range(K)])
     return c, p0
+
+
+# ---------------------------------------------------------------------------
+# Simple-phantom geometry of Sec. 4.1.1 (stand-in: the paper shows the shapes only in
+# figures).  A 20 mm x 20 mm target sits in a computational domain with a sensor layer of
+# `margin` metres on every side; 236 point sensors lie evenly on the square 0.2 mm outside
+# the target boundary.
+
+SIMPLE_TARGET = 20e-3      # target side (m)
+SIMPLE_MARGIN = 0.64e-3    # sensor layer on each side (10 data-grid pixels of 63.7 um)
+SIMPLE_L = SIMPLE_TARGET + 2 * SIMPLE_MARGIN
+
+
+def square_sensors(m: int = 236, offset: float = 0.2e-3, target: float = SIMPLE_TARGET,
+                   margin: float = SIMPLE_MARGIN) -> np.ndarray:
+    """``m`` sensors evenly spaced (by arc length) on the square ``offset`` outside the target.
+
+    Returns ``[m][2]`` (x, y) in metres in the domain frame.
+    """
+    side = target + 2.0 * offset
+    lo = margin - offset
+    s = (np.arange(m) + 0.5) * (4.0 * side / m)
+    xy = np.empty((m, 2))
+    for i, t in enumerate(s):
+        e, u = int(t // side), t % side
+        xy[i] = [(lo + u, lo), (lo + side, lo + u), (lo + side - u, lo + side), (lo, lo + side - u)][e]
+    return xy
+
+
+def _disc(n: int, L: float, cx: float, cy: float, r: float) -> np.ndarray:
+    """Area fraction of each cell inside the disc (4 x 4 sub-samples per cell)."""
+    dx = L / n
+    sub = (np.arange(4) + 0.5) / 4.0
+    acc = np.zeros((n, n))
+    for sy in sub:
+        for sx in sub:
+            x = (np.arange(n) + sx) * dx
+            y = (np.arange(n) + sy) * dx
+            acc += ((x[None, :] - cx) ** 2 + (y[:, None] - cy) ** 2) <= r * r
+    return acc / 16.0
+
+
+def _rect(n: int, L: float, x0: float, x1: float, y0: float, y1: float) -> np.ndarray:
+    dx = L / n
+    sub = (np.arange(4) + 0.5) / 4.0
+    acc = np.zeros((n, n))
+    for sy in sub:
+        for sx in sub:
+            x = (np.arange(n) + sx) * dx
+            y = (np.arange(n) + sy) * dx
+            acc += ((x[None, :] >= x0) & (x[None, :] < x1)) & ((y[:, None] >= y0) & (y[:, None] < y1))
+    return acc / 16.0
+
+
+def simple_phantom_c(kind: str, n: int, L: float = SIMPLE_L, margin: float = SIMPLE_MARGIN) -> np.ndarray:
+    """Speed of sound of the simple phantoms on an n x n grid over the domain of side L.
+
+    kind "circles": nine circular inclusions (1580 m/s, radius 1.6 mm, 3 x 3 lattice with
+    6 mm pitch) in a 1430 m/s background; "water": the same plus a 3 mm water layer
+    (1482 m/s) along the lower target edge; "bone": the circles plus a 6 mm x 2 mm
+    rectangular inclusion of 2500 m/s.  Cells are area-averaged.
+    """
+    c0 = SIMPLE_TARGET / 2.0 + margin
+    c = np.full((n, n), 1430.0)
+    if kind == "water":
+        f = _rect(n, L, 0.0, L, 0.0, margin + 3e-3)
+        c = c * (1.0 - f) + 1482.0 * f
+    for iy in (-1, 0, 1):
+        for ix in (-1, 0, 1):
+            f = _disc(n, L, c0 + 6e-3 * ix, c0 + 6e-3 * iy, 1.6e-3)
+            c = c * (1.0 - f) + 1580.0 * f
+    if kind == "bone":
+        f = _rect(n, L, c0 - 3e-3, c0 + 3e-3, c0 + 2e-3, c0 + 4e-3)
+        c = c * (1.0 - f) + 2500.0 * f
+    return c
+
+
+def simple_phantom_p0(n: int, K: int = 4, seed: int = 0, L: float = SIMPLE_L,
+                      margin: float = SIMPLE_MARGIN) -> np.ndarray:
+    """K initial pressures of circular inclusions (10 Pa) in a zero background.
+
+    Each p0_k holds 4-6 discs of radius 0.6-1.6 mm at seeded positions inside the target.
+    """
+    rng = rng_for(7000 + seed)
+    out = np.zeros((K, n, n))
+    for k in range(K):
+        for _ in range(int(rng.integers(4, 7))):
+            r = rng.uniform(0.6e-3, 1.6e-3)
+            cx, cy = rng.uniform(margin + 2.5e-3, margin + SIMPLE_TARGET - 2.5e-3, size=2)
+            out[k] = np.maximum(out[k], 10.0 * _disc(n, L, cx, cy, r))
+    return out
