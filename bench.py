@@ -219,6 +219,20 @@ def cpu_value(seconds: float, nt_s: int, K_s: int) -> float:
     return 1.0 / (seconds * scale)
 
 
+def max_over_ranks(t_ms: float, device) -> float:
+    """Slowest rank's time: every rank of the process group gets the maximum of t_ms."""
+    import torch
+    import torch.distributed as tdist
+    tt = torch.tensor([t_ms], dtype=torch.float64, device=device)
+    tdist.all_reduce(tt, op=tdist.ReduceOp.MAX)
+    return float(tt.item())
+
+
+def whole_job_rate(world: int, steps: int, t_ms: float) -> float:
+    """Units per second of the whole job: every rank ran `steps` units in at most t_ms."""
+    return world * steps / (t_ms / 1000.0)
+
+
 def run_reference(args, rank):
     if rank != 0:
         return
@@ -345,10 +359,8 @@ def run_ours(args, rank, world, local_rank):
     launches = int(L.pat_kernel_launches() - launches0)
     t_ms = e0.elapsed_time(e1)
     if dist:
-        tt = torch.tensor([t_ms], dtype=torch.float64, device=dev)
-        tdist.all_reduce(tt, op=tdist.ReduceOp.MAX)
-        t_ms = float(tt.item())
-    value = world * args.steps / (t_ms / 1000.0)
+        t_ms = max_over_ranks(t_ms, dev)
+    value = whole_job_rate(world, args.steps, t_ms)
 
     # forward-only throughput (Gcell-steps/s) on the same workload
     yb = torch.empty((K, nt, M), dtype=torch.float32, device=dev)
@@ -397,10 +409,8 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.synchronize()
     e2e_ms = g0.elapsed_time(g1)
     if dist:
-        tt = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
-        tdist.all_reduce(tt, op=tdist.ReduceOp.MAX)
-        e2e_ms = float(tt.item())
-    e2e_val = world * args.steps / (e2e_ms / 1000.0)
+        e2e_ms = max_over_ranks(e2e_ms, dev)
+    e2e_val = whole_job_rate(world, args.steps, e2e_ms)
 
     # roofline of the dominant kernel
     peak, peak_kind = measured_peaks()
