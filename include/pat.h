@@ -109,7 +109,9 @@ int pat_plan_ng(pat_plan plan);
  * (108, 144, 180, 200, 240, 300 = N1 x N2) have five fixed-size variants,
  * all one launch per pass:
  *   0  column and velocity passes on the N1 x N2 factorisation, density
- *      passes on N2 x N1 (4 rows / 4 spectral columns per CTA);
+ *      passes on N2 x N1 (4 rows / 4 spectral columns per CTA); the column
+ *      passes of the forward sweep, which runs alone on the GPU, take 8
+ *      columns per CTA;
  *   1  all passes N1 x N2, 4 rows / 4 columns per CTA;
  *   2  all passes N1 x N2, 8 rows / 2 columns per CTA;
  *   3  as 1 with the row passes' state staged in shared memory by TMA bulk

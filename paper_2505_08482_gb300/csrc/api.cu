@@ -58,7 +58,7 @@ int run_steps(const Launch& L, const Ws& w, int n0, int n1, float* y, float* his
 
 int pat::forward_sweep(pat_plan_s* p, const float* c, const float* p0, float* y, const Ws& w, bool keep,
                        cudaStream_t st) {
-    Launch L{p, st};
+    Launch L{p, st, true};
     RC(launch_medium(L, c, w.cg));
     PAT_CUDA(cudaMemsetAsync(y, 0, size_t(p->K) * p->nt * p->m * sizeof(float), st));
     PAT_CUDA(cudaMemsetAsync(w.flag + 1, 0, sizeof(int), st));   // bounded-wait status of this call
@@ -309,7 +309,7 @@ extern "C" int pat_plan_autotune(pat_plan p, void* ws, size_t ws_bytes, double* 
         if (rc == PAT_OK) rc = vfill(st, tmp, float(p->g.c_ref), size_t(p->ninst) * nn);
     }
     Ws w = resolve(p, ws, grad);
-    Launch L{p, st};
+    Launch L{p, st, true};   // forward-step timing mirrors the forward sweep
     float* c = tmp;
     float* p0 = tmp ? tmp + size_t(p->ninst) * nn : nullptr;
     float* gp0 = tmp ? p0 + size_t(p->K) * nn : nullptr;

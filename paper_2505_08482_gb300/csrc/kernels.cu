@@ -637,7 +637,7 @@ int launch_col(const Launch& L, float2* A, float2* B, int mode, int op, float sc
     const int cls = mode == 0 ? PAT_K_COL_GRAD : (mode == 1 ? PAT_K_COL_PAIR : PAT_K_COL_SUM);
     prof_begin(cls, L.st);
     if (p->fast)
-        p->fast->col(geo(p), L.st, A, B, mode, op, scale);
+        ((L.solo && p->fast->col_solo) ? p->fast->col_solo : p->fast->col)(geo(p), L.st, A, B, mode, op, scale);
     else
         k_col<<<grid, 256, p->smem_col, L.st>>>(geo(p), A, B, mode, op, scale, p->C);
     prof_end(cls, L.st);

@@ -42,6 +42,8 @@ struct FixedOps {
                     const float* p0, float* y, int tstep, float* hist, int hist_slot);
     void (*row_adj_rho)(const Geo&, cudaStream_t, float2*, float2*, float*, float*, float*, const float*,
                         int first, const float* resid, int tstep, const float* hist, int hist_slot);
+    // column pass for passes that run alone on the GPU (nullptr: col)
+    void (*col_solo)(const Geo&, cudaStream_t, float2*, float2*, int mode, int op, float scale);
 };
 
 const FixedOps* fixed_ops_for(int ng, int variant);   // nullptr if no fixed size matches
@@ -740,24 +742,29 @@ struct FixedImpl {
         launch_pdl(kf_row_adj_rho<N1, N2, RR, STAGE>, grid, dim3(RR * F::T), smem_adj, st, true, g, A2, B2, rbx,
                    rby, cbar, cg, first, resid, tstep, hist, slot);
     }
-    static FixedOps ops() { return FixedOps{F::N, RR, CC, &configure, &col, &row_u, &row_rho, &row_adj_rho}; }
+    static FixedOps ops() {
+        return FixedOps{F::N, RR, CC, &configure, &col, &row_u, &row_rho, &row_adj_rho, nullptr};
+    }
 };
 
 // A variant whose pass kinds come from different tile shapes / factorisations of the same
-// Ng (the half spectra in global memory have one layout): column passes from C, velocity
-// row passes from U, density row passes from R, adjoint density row passes from J.
-template <class C, class U, class R, class J>
+// Ng (the half spectra in global memory have one layout): column passes from C (from CS when
+// the pass runs alone on the GPU), velocity row passes from U, density row passes from R,
+// adjoint density row passes from J.
+template <class C, class U, class R, class J, class CS = C>
 struct MixedImpl {
-    static_assert(C::F::N == U::F::N && C::F::N == R::F::N && C::F::N == J::F::N, "one grid side");
+    static_assert(C::F::N == U::F::N && C::F::N == R::F::N && C::F::N == J::F::N && C::F::N == CS::F::N,
+                  "one grid side");
     static int configure() {
         int rc = C::configure();
         if (rc == PAT_OK) rc = U::configure();
         if (rc == PAT_OK) rc = R::configure();
         if (rc == PAT_OK) rc = J::configure();
+        if (rc == PAT_OK) rc = CS::configure();
         return rc;
     }
     static FixedOps ops() {
-        return FixedOps{C::F::N, 0, 0, &configure, &C::col, &U::row_u, &R::row_rho, &J::row_adj_rho};
+        return FixedOps{C::F::N, 0, 0, &configure, &C::col, &U::row_u, &R::row_rho, &J::row_adj_rho, &CS::col};
     }
 };
 

@@ -1,6 +1,7 @@
 // Fixed-size passes for the grid side Ng = 300 = 20 x 15.  Variants: 0 column and velocity
 // passes on the 20 x 15 factorisation, density passes on 15 x 20 (fewer registers where the
-// state is preloaded); 1 all 20 x 15, 4 rows / 4 columns per CTA; 2 the same with 8 rows /
+// state is preloaded), and 8-column tiles for the column passes of the forward sweep, which
+// runs alone on the GPU; 1 all 20 x 15, 4 rows / 4 columns per CTA; 2 the same with 8 rows /
 // 2 columns; 3 state staged in shared memory by TMA bulk copies; 4 all 15 x 20.
 #include "kfixed.cuh"
 
@@ -11,10 +12,11 @@ using A4 = FixedImpl<20, 15, 4, 4, false>;
 using A8 = FixedImpl<20, 15, 8, 2, false>;
 using S4 = FixedImpl<20, 15, 4, 4, true>;
 using B4 = FixedImpl<15, 20, 4, 4, false>;
+using C8 = FixedImpl<20, 15, 4, 8, false>;
 }  // namespace
 
 const FixedOps* fixed_ops_300(int v) {
-    static const FixedOps ops[] = {MixedImpl<A4, A4, B4, B4>::ops(), A4::ops(), A8::ops(), S4::ops(), B4::ops()};
+    static const FixedOps ops[] = {MixedImpl<A4, A4, B4, B4, C8>::ops(), A4::ops(), A8::ops(), S4::ops(), B4::ops()};
     return (v >= 0 && v < 5) ? &ops[v] : nullptr;
 }
 
