@@ -122,7 +122,7 @@ def pml_auto(n, min_pml=20):
 class ClockSampler:
     """nvidia-smi clock / throttle-reason sampling during the timed region."""
 
-    Q = ("clocks.sm,clocks.max.sm,power.draw,utilization.gpu,clocks_event_reasons.active,"
+    Q = ("timestamp,clocks.sm,clocks.max.sm,power.draw,utilization.gpu,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
@@ -130,6 +130,15 @@ class ClockSampler:
         self.idx = gpu_index
         self.proc = None
         self.path = None
+        self.t0 = self.t1 = None
+
+    def mark(self, begin: bool):
+        """Host time of the start or the end of the timed region (samples outside are dropped)."""
+        import datetime
+        if begin:
+            self.t0 = datetime.datetime.now()
+        else:
+            self.t1 = datetime.datetime.now()
 
     def start(self):
         fd, self.path = tempfile.mkstemp(suffix=".csv")
@@ -149,14 +158,18 @@ class ClockSampler:
             self.proc.wait(timeout=5)
         except subprocess.TimeoutExpired:
             self.proc.kill()
+        import datetime
         rows = []
         for line in open(self.path):
             parts = [p.strip() for p in line.split(",")]
-            if len(parts) < 9:
+            if len(parts) < 10:
                 continue
             try:
-                rows.append(dict(sm=float(parts[0]), smax=float(parts[1]), util=float(parts[3]),
-                                 hw=parts[5], hwt=parts[6], swt=parts[7], pcap=parts[8]))
+                ts = datetime.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f")
+                if (self.t0 and ts < self.t0) or (self.t1 and ts > self.t1):
+                    continue
+                rows.append(dict(sm=float(parts[1]), smax=float(parts[2]), util=float(parts[4]),
+                                 hw=parts[6], hwt=parts[7], swt=parts[8], pcap=parts[9]))
             except ValueError:
                 continue
         os.unlink(self.path)
@@ -329,30 +342,39 @@ def run_ours(args, rank, world, local_rank):
         grad_eval()
     dom_ms, dom_cnt = ctypes_read(L)
     B.check(L.pat_timing_enable(0, 0, 1), "pat_timing_enable")
+    # the clock sampler starts here, so that its own start-up (NVML initialisation on a fresh
+    # machine) falls before the timed region; it keeps only the samples inside the region
+    sampler = ClockSampler(local_rank)
+    sampler.start()
     if not args.no_graphs:
         plan.set_graphs(True)
-        for _ in range(2):   # capture, then one replay before timing
-            grad_eval()
+    # the timed loop's own body (flush, evaluation) until at least 3 iterations and 2 s have
+    # passed: a fresh machine's first process otherwise sees slower first seconds of replays
+    t_w, n_w = time.perf_counter(), 0
+    while n_w < 3 or (time.perf_counter() - t_w < 2.0 and n_w < 64):
+        flush.zero_()
+        grad_eval()
         torch.cuda.synchronize()
+        n_w += 1
 
     dist = world > 1
     if dist:
         import torch.distributed as tdist
-    sampler = ClockSampler(local_rank)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     launches0 = L.pat_kernel_launches()
     # kernel launches before the timed region (the skip count of an ncu launch list of it)
     print(f"launches_before_timed={launches0}", file=sys.stderr, flush=True)
-    sampler.start()
     if dist:
         tdist.barrier()
     torch.cuda.synchronize()
+    sampler.mark(True)
     e0.record(stream)
     for _ in range(args.steps):
         flush.zero_()
         grad_eval()
     e1.record(stream)
     torch.cuda.synchronize()
+    sampler.mark(False)
     if dist:
         tdist.barrier()
     clocks = sampler.stop()
