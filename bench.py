@@ -348,10 +348,12 @@ def run_ours(args, rank, world, local_rank):
     sampler.start()
     if not args.no_graphs:
         plan.set_graphs(True)
-    # the timed loop's own body (flush, evaluation) until at least 3 iterations and 2 s have
-    # passed: a fresh machine's first process otherwise sees slower first seconds of replays
+    # the timed loop's own body (flush, evaluation): 3 iterations, and with graphs until 2 s
+    # have passed (a fresh machine's first process otherwise sees slower first seconds of
+    # replays); eager runs keep a fixed count so that profiler runs launch the same kernels
     t_w, n_w = time.perf_counter(), 0
-    while n_w < 3 or (time.perf_counter() - t_w < 2.0 and n_w < 64):
+    floor_s = 0.0 if args.no_graphs else 2.0
+    while n_w < 3 or (time.perf_counter() - t_w < floor_s and n_w < 64):
         flush.zero_()
         grad_eval()
         torch.cuda.synchronize()
