@@ -395,10 +395,10 @@ typedef struct {
  * alone.  Synchronises the stream once per evaluation round. */
 int pat_reconstruct_batched(const pat_recon_cfg* cfg, int ninst, const pat_instance* inst, void* stream);
 
-/* ---- learned warm start (spec extension; the paper has no network) ----
+/* ---- learned warm start (an extension: the paper has no network) ----
  * A U-Net mapping K back-projected images (adjoint solves at a constant
  * speed of sound, i.e. pat_vjp with c = c0) to an initial speed-of-sound map
- * for pat_reconstruct; the iterative solve stays the judge of the result.
+ * for pat_reconstruct; the iterative solve still decides the result.
  * Encoder level l (0..levels-1): two 3x3 convolutions + ReLU with base*2^l
  * channels and 2x2 max pooling between levels; decoder: nearest 2x
  * upsampling, concatenation [upsampled, encoder] and two 3x3 convolutions +

@@ -5,7 +5,7 @@ the forward operator at a constant speed of sound c0, computed by the
 library's adjoint kernels through pat_vjp), normalised by their common peak;
 the target is (c_true - c0) / c_scale.  The network runs in the library's
 BF16 tensor-core kernels (pat_unet_*); the plain iterative reconstruction
-remains the fallback and the judge of the error.
+remains the fallback and the arbiter of the error.
 """
 from __future__ import annotations
 
