@@ -514,7 +514,7 @@ def run_batch(args):
         for (i, K), c in zip(members, cs):
             yk = ps.add_noise(y[k0:k0 + K], ps.rng_for(4000 + i))
             data[i] = dict(y_meas=f32(yk), w=f32(ps.noise_weights(yk)),
-                           c_init=f32(np.full((n, n), 0.5 * (c.min() + c.max()))), c_true=c)
+                           c_init=f32(np.full((n, n), 0.5 * (c.min() + c.max()))))
             k0 += K
         data[("cfg", n)] = ReconConfig(levels=(n // 2, n), L=n * dx, dt_data=gs.dt, nt_data=nt, sensors_xy=xy, K=1,
                                        iters=args.batch_iters, mem=20, ckpt_every=32, autotune=True)

@@ -301,7 +301,7 @@ typedef struct {
     double alpha0;
     double c1;
     double sigma_p0;
-    int autotune;   /* nonzero: run pat_plan_autotune on every level's plan */
+    int autotune;   /* nonzero: run pat_plan_autotune on every level's plan (forward-step timing) */
     /* Ornstein-Uhlenbeck prior terms of Eq. Minimised_functional (Sec. 4.1.2):
      * prior_tau > 0 (m) adds, on every level's grid, 1/2 |L_c (c - eta_c)|^2
      * and 1/2 |L_p0 (p0_k - eta_p0)|^2 for every k to J (see pat_prior_eval;

@@ -230,7 +230,9 @@ int Batch::level(int li, const float* const* xprev, int nprev) {
     RC(pat_plan_create_batched(&plan, &g, M, cfg.h_sensor_xy, ni, Ks.data(), cfg.ckpt_every));
     wsb = pat_workspace_bytes(plan, PAT_WS_GRADIENT);
     RC(alloc(reinterpret_cast<char**>(&ws), wsb));
-    if (cfg.autotune) RC(pat_plan_autotune(plan, ws, wsb, nullptr, st));
+    // forward-step timing (a short run on the forward part of the workspace): the gradient
+    // timing of six whole evaluations per level would cost more than it saves here
+    if (cfg.autotune) RC(pat_plan_autotune(plan, ws, pat_workspace_bytes(plan, PAT_WS_FORWARD), nullptr, st));
     if (prior) pat_prior_destroy(prior);
     prior = nullptr;
     if (cfg.prior_tau > 0) {
