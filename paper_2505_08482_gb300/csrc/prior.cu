@@ -51,7 +51,7 @@ struct pat_prior_s {
 namespace {
 
 constexpr int kDotBlocks = 64;
-enum { SC_RS = 0, SC_BB, SC_ALPHA, SC_BETA, SC_ETA, SC_COEF, SC_ISIG2, SC_TMP, kSc };
+enum { SC_RS = 0, SC_BB, SC_ALPHA, SC_BETA, SC_ETA, SC_COEF, SC_ISIG2, kSc };
 
 // ---- transforms ----------------------------------------------------------
 // rows y < n of the padded fields (2p, 2p+1) -> row FFT -> W[p][y][:]
