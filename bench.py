@@ -93,6 +93,8 @@ def parse():
     ap.add_argument("--roofline-k", type=int, default=0,
                     help="per-pass bandwidth of forward steps with this many data sets on the headline grid "
                          "(working set beyond L2 for K >= 64); uses --nt and --variant")
+    ap.add_argument("--prior-cost", action="store_true",
+                    help="cost of the Ornstein-Uhlenbeck prior terms on the headline grid (9 fields)")
     ap.add_argument("--table2", action="store_true",
                     help="simple-phantom experiment of Sec. 4.1: data on a fine grid (no inverse crime), joint "
                          "reconstruction with K=4 data sets against K=1 over four multigrid levels")
@@ -653,6 +655,48 @@ def run_roofline_k(args):
                       "kernel_source_hash": kernel_source_hash()}), flush=True)
 
 
+def run_prior_cost(args):
+    """Time one evaluation of the prior terms (value and gradient) for c and the 8 p0 fields
+    of the headline workload on its 256 x 256 grid (dx 0.1 mm, tau 1.5 mm): cold start, then
+    started from that solution after adding white noise of 0.1 % of each field's peak (a rough
+    change: it excites the high spatial frequencies, where Xi's eigenvalues are smallest)."""
+    import numpy as np
+    import torch
+
+    import pat_synth as ps
+    import paper_2505_08482_gb300 as pkg
+    from paper_2505_08482_gb300.solver import Prior
+
+    pkg.build()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(0)
+    w, _ = inputs(0)
+    n, K = WL["n"], WL["K"]
+    f32 = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float32, device=dev)
+    x = f32(np.concatenate([w.p0_true, w.c_true[None]]))
+    lo, hi = float(w.c_true.min()), float(w.c_true.max())
+    eta = [0.5] * K + [0.5 * (lo + hi)]
+    sig = [0.25] * K + [0.25 * (hi - lo)]
+    pr = Prior(n, WL["dx"], 1.5e-3, K + 1, device=dev)
+    out = {}
+    for _ in range(2):                       # first launches of the kernels
+        pr.eval(x, eta, sig, tol=1e-5, maxit=500)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    v, g, z, it = pr.eval(x, eta, sig, tol=1e-5, maxit=500)
+    out["cold"] = {"ms": 1000 * (time.perf_counter() - t0), "iterations": it}
+    torch.manual_seed(0)
+    x2 = x + 1e-3 * torch.randn_like(x) * x.abs().amax(dim=(1, 2), keepdim=True)
+    t0 = time.perf_counter()
+    v2, g2, z2, it2 = pr.eval(x2, eta, sig, z=z, tol=1e-5, maxit=500)
+    out["warm_after_white_noise"] = {"ms": 1000 * (time.perf_counter() - t0), "iterations": it2}
+    print(json.dumps({"metric": "Ornstein-Uhlenbeck prior terms: ms per evaluation (value and gradient)",
+                      "unit": "ms", "n_gpus": 1, "dtype": "f32", "data": "synthetic",
+                      "config": {"workload": f"{n}x{n} grid, dx 0.1 mm, tau 1.5 mm, {K + 1} fields (8 p0 + c), "
+                                             "PCG to a relative residual of 1e-5"},
+                      "results": out}), flush=True)
+
+
 def run_table2(args):
     """Simple-phantom experiment (Sec. 4.1, Table 2 trend) on the paper's geometry.
 
@@ -818,6 +862,9 @@ def main():
         return
     if args.table2:
         run_table2(args)
+        return
+    if args.prior_cost:
+        run_prior_cost(args)
         return
     if world > 1:
         import torch
