@@ -138,7 +138,8 @@ __device__ __forceinline__ void col_mults(const Geo& g, int kx, int ky, int op, 
 
 // ---------------------------------------------------------------------------
 // column pass; mode 0: A -> (MX A, MY A) into (A, B); 1: (A, B) -> (MX A, MY B); 2: MX A + MY B -> A.
-// The two fields (or the two outputs) of a column are handled by separate threads (f = 0, 1).
+// The two fields (or the two outputs) of a column are handled by separate threads (f = 0, 1);
+// in mode 0 they share the first transform stage.
 // Tables and twiddles are staged before the dependency wait, the columns read after it.
 template <int N1, int N2, int CC>
 __global__ void __launch_bounds__(2 * CC * Fft2<N1, N2>::T) kf_col(Geo g, float2* __restrict__ A,
@@ -178,8 +179,10 @@ __global__ void __launch_bounds__(2 * CC * Fft2<N1, N2>::T) kf_col(Geo g, float2
     });
     pdl_wait_then_release();
     float2* Zmine = Zf + f * F::ZS * CC + c;
+    // mode 0 has one input: the f = 1 threads read the f = 0 threads' first transform stage
+    const bool own_fwd = mode != 0 || f == 0;
     float2 a[N1];
-    if (idx < N2) {
+    if (idx < N2 && own_fwd) {
         const float2* src = (mode == 0 || f == 0) ? A : B;
         static_for<0, N1>([&](auto I) {
             constexpr int n1 = decltype(I)::value;
@@ -187,12 +190,12 @@ __global__ void __launch_bounds__(2 * CC * Fft2<N1, N2>::T) kf_col(Geo g, float2
         });
     }
     __syncthreads();   // twiddles and multipliers staged by all threads
-    if (idx < N2) F::template fwd_a<CC>(a, idx, Zmine, tw);
+    if (idx < N2 && own_fwd) F::template fwd_a<CC>(a, idx, Zmine, tw);
     __syncthreads();
     float2 b[N2];
     const float2* Mm = (f == 0) ? MX : MY;
     if (idx < N1) {
-        F::template fwd_b_load<CC>(b, idx, Zmine);
+        F::template fwd_b_load<CC>(b, idx, own_fwd ? Zmine : Zf + c);
         F::fwd_b(b);
         static_for<0, N2>([&](auto I) {
             constexpr int k2 = decltype(I)::value;
