@@ -51,7 +51,8 @@ struct Inst {
     size_t V, n0;               // vector length, length of the p0 block
     float *x, *z, *g, *d, *xt, *zt, *gt, *q, *psi;
     float* ct = nullptr;        // true c resampled to the level (E_c tracking), or null
-    float* zp = nullptr;        // Xi^{-1} (x - eta) of the last prior evaluation (its PCG warm start)
+    float* zp = nullptr;        // Xi^{-1} (x - eta) at the accepted point x (the prior solves' warm start)
+    float* zpt = nullptr;       // the same at the trial point xt
     bool zp_warm = false;
     std::vector<float*> S, Y;   // ring of curvature pairs
     double* lam;                // [mem] device
@@ -164,9 +165,14 @@ int Batch::evaluate(bool grad, bool trial) {
             sig[s.K] = cfg.prior_sigma_c;
             gs[s.K] = scs;
             float* gdst = grad ? (trial ? s.gt : s.g) : nullptr;
-            RC(pat_prior_eval(prior, trial ? s.xt : s.x, s.K + 1, eta.data(), sig.data(), gs.data(), s.zp, gdst,
+            // every solve starts from the accepted point's solution, so that an instance's
+            // results do not depend on evaluations made for other instances of a batch
+            float* zdst = trial ? s.zpt : s.zp;
+            if (trial && s.zp_warm)
+                PAT_CUDA(cudaMemcpyAsync(s.zpt, s.zp, s.V * sizeof(float), cudaMemcpyDeviceToDevice, st));
+            RC(pat_prior_eval(prior, trial ? s.xt : s.x, s.K + 1, eta.data(), sig.data(), gs.data(), zdst, gdst,
                               dJ + i, 1e-5, 500, s.zp_warm ? 1 : 0, nullptr, st));
-            s.zp_warm = true;
+            if (!trial) s.zp_warm = true;
         }
     }
     PAT_CUDA(cudaMemcpyAsync(hJ.data(), dJ, ni * sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -272,7 +278,10 @@ int Batch::level(int li, const float* const* xprev, int nprev) {
         }
         RC(alloc(&s.lam, memsz));
         RC(alloc(&s.rho, memsz));
-        if (prior) RC(alloc(&s.zp, s.V));
+        if (prior) {
+            RC(alloc(&s.zp, s.V));
+            RC(alloc(&s.zpt, s.V));
+        }
         // x0 = resample of the previous level (or of the initial guess); z = P(x0 / sigma)
         RC(vresample(st, xprev[i], s.xt, s.K + 1, nprev, N));
         RC(vblockscale(st, s.zt, s.xt, s.V, s.n0, float(sp), float(sc_c), 1));
@@ -442,6 +451,7 @@ int Batch::level(int li, const float* const* xprev, int nprev) {
             std::swap(s.z, s.zt);
             std::swap(s.x, s.xt);
             std::swap(s.g, s.gt);
+            std::swap(s.zp, s.zpt);
             s.J = Jn;
             if (rel < cfg.rtol) s.active = false;
             // a tracked instance leaves a level (the last one: stops) once E_c reaches its target

@@ -102,7 +102,8 @@ def test_autotune_selects_a_variant_with_identical_physics():
     assert rel_l2(y, plan.forward(_dev(c), _dev(p0)).cpu().numpy()) <= 1e-5
 
 
-def test_batched_reconstruction_equals_single_reconstructions():
+@pytest.mark.parametrize("with_prior", [False, True])
+def test_batched_reconstruction_equals_single_reconstructions(with_prior):
     from oracle.forward import forward
     from oracle.sensors import sensor_matrix
     from tests._problems import oracle_grid
@@ -118,6 +119,9 @@ def test_batched_reconstruction_equals_single_reconstructions():
         insts.append(dict(y_meas=_dev(y), w=_dev(ps.noise_weights(y)), c_init=_dev(np.full((n, n), 1510.0))))
     cfg = ReconConfig(levels=(32, 64), L=n * 1e-4, dt_data=g.dt, nt_data=g.nt, sensors_xy=xy, K=1, iters=4,
                       mem=5, ckpt_every=32)
+    if with_prior:   # Ornstein-Uhlenbeck terms: each instance's solves must not see the others'
+        cfg.prior_tau, cfg.prior_eta_c, cfg.prior_sigma_c = 1.5e-3, 1510.0, 50.0
+        cfg.prior_eta_p0, cfg.prior_sigma_p0 = 0.5, 0.25
     res, ms = reconstruct_batched(cfg, insts)
     for ins, (c_b, p0_b, rows_b, st_b) in zip(insts, res):
         cfg.K = int(ins["y_meas"].shape[0])
