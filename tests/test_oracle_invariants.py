@@ -1,5 +1,6 @@
 """Invariants of the oracle: energy (P3), linearity (P6), exactness of interpolants."""
 import numpy as np
+import pytest
 
 from oracle import forward as F
 from oracle.grid import Grid
@@ -71,3 +72,19 @@ def test_time_interp_exact_on_linear_signals():
     td = np.arange(100) * dt_d
     assert np.abs(out[0, :, 0] - (1.0 + 3e7 * td)).max() < 1e-12
     assert np.abs(out[0, :, 1] - (-2.0 + 1e6 * td)).max() < 1e-12
+
+
+def test_relative_error_values_of_eq_relative_error():
+    """Eq. (RelativeError): 100 % ||true - rec|| / ||true||, the Euclidean norm over all cells."""
+    from oracle.metrics import relative_error
+    rng = ps.rng_for(4)
+    true = 1500.0 + 40.0 * rng.standard_normal((12, 12))
+    assert relative_error(true, true) == 0.0
+    assert relative_error(true, 0.97 * true) == pytest.approx(3.0, rel=1e-12)
+    assert relative_error(true, np.zeros_like(true)) == pytest.approx(100.0, rel=1e-12)
+    # an error orthogonal to the true field adds in quadrature: 3-4-5 on two cells
+    t2 = np.array([[4.0, 0.0]])
+    assert relative_error(t2, np.array([[4.0, 3.0]])) == pytest.approx(75.0, rel=1e-12)
+    # a norm over cells, not a mean of per-cell ratios: one wrong cell of two
+    assert relative_error(np.array([1.0, 10.0]), np.array([0.0, 10.0])) == pytest.approx(
+        100.0 / np.sqrt(101.0), rel=1e-12)
