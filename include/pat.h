@@ -131,7 +131,9 @@ int pat_plan_variant(pat_plan plan);
  * a given set of buffers and kernel variant is captured into a CUDA graph and
  * every later call with the same buffers replays it (one launch for the
  * whole call).  Buffers are keyed by address: a caller that reuses
- * addresses for new data gets the new data.  enable = 0 frees the graphs. */
+ * addresses for new data gets the new data.  A plan keeps at most 16
+ * graphs; capturing another one first frees the least recently replayed.
+ * enable = 0 frees the graphs. */
 int pat_plan_set_graphs(pat_plan plan, int enable);
 
 /* Autotuner: times every variant of the plan (generic and fixed-size) on

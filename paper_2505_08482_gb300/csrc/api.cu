@@ -174,8 +174,16 @@ int with_graph(pat_plan_s* p, int kind, const std::array<const void*, 10>& key, 
         if (g.kind == kind && g.variant == p->variant && g.key == key && g.ws_bytes == ws_bytes) {
             PAT_CUDA(cudaGraphLaunch(g.exec, st));
             add_launches(g.launches);
+            g.last_use = ++p->graph_clock;
             return PAT_OK;
         }
+    if (p->graphs.size() >= pat_plan_s::kMaxGraphs) {
+        // an executable graph still in flight is released when its work completes
+        auto lru = std::min_element(p->graphs.begin(), p->graphs.end(),
+                                    [](const auto& a, const auto& b) { return a.last_use < b.last_use; });
+        cudaGraphExecDestroy(lru->exec);
+        p->graphs.erase(lru);
+    }
     const unsigned long long l0 = launches_so_far();
     PAT_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
     int rc = body();
@@ -191,7 +199,7 @@ int with_graph(pat_plan_s* p, int kind, const std::array<const void*, 10>& key, 
     cudaGraphDestroy(graph);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
     const unsigned long long n = launches_so_far() - l0;
-    p->graphs.push_back(pat_plan_s::Graph{kind, p->variant, key, ws_bytes, exec, n});
+    p->graphs.push_back(pat_plan_s::Graph{kind, p->variant, key, ws_bytes, exec, n, ++p->graph_clock});
     PAT_CUDA(cudaGraphLaunch(exec, st));
     return PAT_OK;
 }

@@ -80,16 +80,20 @@ struct pat_plan_s {
     // host bookkeeping: the workspace whose history holds the last segment
     const void* hist_valid_ws;
     int device;
-    // captured CUDA graphs of whole calls, keyed by call kind, buffers and variant
+    // captured CUDA graphs of whole calls, keyed by call kind, buffers and variant;
+    // at most kMaxGraphs are kept, the least recently replayed one is dropped first
+    static constexpr size_t kMaxGraphs = 16;
     struct Graph {
         int kind, variant;
         std::array<const void*, 10> key;
         size_t ws_bytes;
         cudaGraphExec_t exec;
         unsigned long long launches;
+        unsigned long long last_use;
     };
     bool use_graphs;
     std::vector<Graph> graphs;
+    unsigned long long graph_clock;
     // second stream and events of the reverse sweep (recompute overlapped with the adjoint)
     cudaStream_t side;
     cudaEvent_t ev_start, ev_rec[2], ev_adj[2];

@@ -216,6 +216,7 @@ extern "C" int pat_plan_create_batched(pat_plan* out, const pat_grid* g, int m, 
     p->nseg = (g->nt + p->s_eff - 1) / p->s_eff;
     p->hist_valid_ws = nullptr;
     p->use_graphs = false;
+    p->graph_clock = 0;
     p->side = nullptr;
     p->ev_start = p->ev_rec[0] = p->ev_rec[1] = p->ev_adj[0] = p->ev_adj[1] = nullptr;
     cudaGetDevice(&p->device);

@@ -87,6 +87,30 @@ def test_graph_replay_equals_direct_calls():
     plan.set_graphs(False)
 
 
+def test_graph_cache_is_bounded_and_recaptures_evicted_calls():
+    """20 output buffers give 20 keys: the plan keeps 16 graphs, a call whose graph was
+    dropped is captured again, and every replay equals the direct call."""
+    n = 40
+    xy = ps.circle_sensors(n, 12, 1e-4)
+    gp = grid_params(n, 60)
+    (c, p0), = _instances(n, [1], 60, seed=5)
+    plan = gpu_plan(gp, xy, 1, ckpt_every=16)
+    cd, pd = _dev(c), _dev(p0)
+    y_ref = plan.forward(cd, pd).clone()
+    plan.set_graphs(True)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        ys = [torch.full_like(y_ref, float("nan")) for _ in range(20)]
+        for rep in range(2):    # captures (with evictions), then recaptures of the dropped ones
+            for y in ys:
+                plan.forward(cd, pd, y=y, stream=stream)
+            stream.synchronize()
+            for y in ys:
+                assert torch.equal(y, y_ref)
+                y.fill_(float("nan"))
+    plan.set_graphs(False)
+
+
 def test_autotune_selects_a_variant_with_identical_physics():
     n = 128
     xy = ps.circle_sensors(n, 32, 1e-4)
