@@ -34,6 +34,9 @@
  *   - Return value: PAT_OK (0) or a negative PAT_E* code; pat_last_error()
  *     gives a message for the calling thread.  Arguments are validated
  *     before anything is launched.
+ *   - A plan is used by one host thread at a time (it holds its graph
+ *     cache, its second stream and the record of which workspace keeps the
+ *     last pressure history); distinct plans may run on distinct threads.
  */
 #ifndef PAT_H
 #define PAT_H
