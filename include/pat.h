@@ -37,6 +37,9 @@
  *   - A plan is used by one host thread at a time (it holds its graph
  *     cache, its second stream and the record of which workspace keeps the
  *     last pressure history); distinct plans may run on distinct threads.
+ *     Calls that share a workspace must be ordered on the GPU (issued on
+ *     one stream, or the caller synchronises between streams): a workspace
+ *     holds the running state of the time stepping.
  */
 #ifndef PAT_H
 #define PAT_H

@@ -336,14 +336,16 @@ extern "C" int pat_plan_create_batched(pat_plan* out, const pat_grid* g, int m, 
         {p->t.kinst, kinst.data(), K * sizeof(int)},
         {p->t.kfirst, kfirst.data(), (ninst + 1) * sizeof(int)},
     };
-    for (const Cp& c : cps) {
-        e = cudaMemcpy(c.dst, c.src, c.n, cudaMemcpyHostToDevice);
-        if (e != cudaSuccess) {
-            int rc = cuda_fail(e, "cudaMemcpy(plan tables)");
-            cudaFree(p->dev);
-            delete p;
-            return rc;
-        }
+    for (const Cp& c : cps)
+        if (e == cudaSuccess) e = cudaMemcpy(c.dst, c.src, c.n, cudaMemcpyHostToDevice);
+    // copies from pageable memory may still be in flight when cudaMemcpy returns, and the
+    // caller's non-blocking streams are not ordered after the legacy stream: wait for them
+    if (e == cudaSuccess) e = cudaStreamSynchronize(cudaStreamLegacy);
+    if (e != cudaSuccess) {
+        int rc = cuda_fail(e, "cudaMemcpy(plan tables)");
+        cudaFree(p->dev);
+        delete p;
+        return rc;
     }
     p->R = 8;
     p->C = 4;

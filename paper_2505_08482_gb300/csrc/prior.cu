@@ -431,6 +431,9 @@ extern "C" int pat_prior_create(int n, double dx, double tau, int max_fields, pa
     if (e == cudaSuccess) e = cudaMemcpy(p->tw, htw.data(), M * sizeof(float2), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(p->lam, hl.data(), hl.size() * sizeof(float), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(p->ilam, hi.data(), hi.size() * sizeof(float), cudaMemcpyHostToDevice);
+    // copies from pageable memory may still be in flight when cudaMemcpy returns, and the
+    // caller's non-blocking streams are not ordered after the legacy stream: wait for them
+    if (e == cudaSuccess) e = cudaStreamSynchronize(cudaStreamLegacy);
     const void* kerns[] = {(const void*)k_pr_rows_fwd, (const void*)k_pr_rows_inv};
     for (const void* f : kerns)
         if (e == cudaSuccess) e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, int(p->smem_rows));

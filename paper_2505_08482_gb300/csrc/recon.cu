@@ -429,7 +429,7 @@ int Batch::level(int li, const float* const* xprev, int nprev) {
             const double sy = hs(i, S_SY), ss = hs(i, S_SS), yy = hs(i, S_YY);
             if (sy > 1e-10 * std::sqrt(ss) * std::sqrt(yy)) {
                 const double rho = 1.0 / sy;
-                PAT_CUDA(cudaMemcpy(s.rho + slot, &rho, sizeof(double), cudaMemcpyHostToDevice));
+                PAT_CUDA(cudaMemcpyAsync(s.rho + slot, &rho, sizeof(double), cudaMemcpyHostToDevice, st));
                 RC(set_scalar(i, S_H0, sy / yy));
                 s.have_h0 = true;
                 if (cfg.mem > 0) {

@@ -71,6 +71,9 @@ def test_graph_replay_equals_direct_calls():
     w = _dev(np.array([1.0, 3.0]))
     y_ref = plan.forward(cd, pd).clone()
     J_ref, g_ref, c_ref = [t.clone() for t in plan.adjoint_grad(cd, pd, ym, w)]
+    # the reference calls used the plan's workspaces on the default stream: the replays on
+    # another stream share them and must not start before those calls end
+    torch.cuda.synchronize()
     plan.set_graphs(True)
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
@@ -97,6 +100,7 @@ def test_graph_cache_is_bounded_and_recaptures_evicted_calls():
     plan = gpu_plan(gp, xy, 1, ckpt_every=16)
     cd, pd = _dev(c), _dev(p0)
     y_ref = plan.forward(cd, pd).clone()
+    torch.cuda.synchronize()   # the replays on another stream share the plan's workspace
     plan.set_graphs(True)
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
