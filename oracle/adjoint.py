@@ -2,7 +2,7 @@
 
 Objective, data term of Eq. (Minimised_functional):
     J = sum_k 1/2 || L_e^k (y_k - f_k(x)) ||^2 = sum_k w_k/2 || S p_k - y_k ||^2
-with L_e^T L_e = w_k I (noise std 1 % of the peak-to-peak amplitude, Sec. 4.1.2).
+with L_e^T L_e = w_k I (noise std = 1 % of each data set's peak-to-peak value, Sec. 4.1.2).
 
 The paper computes the gradient with the adjoint-state method: the adjoint
 wave equation driven by the time-reversed weighted residual (Eq.

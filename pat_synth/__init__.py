@@ -9,8 +9,8 @@ as an input.
 The paper's phantoms and breast data are not available, so the workloads are
 stand-ins that follow the value ranges of Sec. 4: speed of sound of soft tissue
 (inclusions 1400-1650 m/s in a 1500 m/s background, cf. the 1430/1580 m/s
-phantom of Sec. 4.1.1), 1 % additive Gaussian noise relative to the
-peak-to-peak amplitude of each data set (Sec. 4.1.1), and point sensors.
+phantom of Sec. 4.1.1), additive Gaussian noise whose standard deviation is 1 %
+of each data set's peak-to-peak value (Sec. 4.1.1), and point sensors.
 """
 from .phantoms import (ellipse_phantom, blob_p0, vessel_p0, circle_sensors,
                        add_noise, noise_weights, workload, Workload, rng_for,

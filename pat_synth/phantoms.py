@@ -120,7 +120,7 @@ def add_noise(y_clean: np.ndarray, rng: np.random.Generator, rel: float = 0.01) 
     """Additive Gaussian noise, std = ``rel`` x peak-to-peak of each data set.
 
     ``y_clean`` is ``[K][Nt][M]``; data set k gets its own standard deviation
-    (Sec. 4.1.1: 1 % of the peak-to-peak amplitude of the simulated data).
+    (Sec. 4.1.1: standard deviation 1 % of the clean data set's peak-to-peak value).
     """
     y = np.asarray(y_clean, dtype=np.float64)
     out = np.empty_like(y)
@@ -133,8 +133,8 @@ def add_noise(y_clean: np.ndarray, rng: np.random.Generator, rel: float = 0.01) 
 def noise_weights(y_noisy: np.ndarray, rel: float = 0.01) -> np.ndarray:
     """Per-data-set weights w_k = 1 / sigma_k^2 with sigma_k = rel x p2p(noisy y_k).
 
-    The noise model of the reconstruction uses the peak-to-peak amplitude of
-    the noisy signal (Sec. 4.1.2); L_e^T L_e = w_k I.
+    For the reconstruction the noise level is taken from the noisy data's
+    peak-to-peak value (Sec. 4.1.2); L_e^T L_e = w_k I.
     """
     y = np.asarray(y_noisy, dtype=np.float64)
     w = np.empty(y.shape[0])
