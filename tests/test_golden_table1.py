@@ -7,7 +7,6 @@
 """
 import os
 
-import numpy as np
 import pytest
 
 from oracle.grid import time_step, is_smooth

@@ -1,5 +1,4 @@
 """Learned warm start pipeline: solver-generated pairs, training, E_c-tracked reconstruction."""
-import numpy as np
 import pytest
 
 torch = pytest.importorskip("torch")

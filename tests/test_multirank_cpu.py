@@ -8,7 +8,6 @@ different seeded inputs per rank.
 import os
 import socket
 
-import numpy as np
 import pytest
 
 torch = pytest.importorskip("torch")
