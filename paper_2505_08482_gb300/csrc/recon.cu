@@ -479,7 +479,7 @@ int Batch::run() {
     // initial guesses on the finest grid, stacked [K+1][Nf][Nf] per instance
     std::vector<const float*> xprev(ni);
     for (int i = 0; i < ni; ++i) {
-        float* xf;
+        float* xf = nullptr;
         RC(alloc(&xf, size_t(ins[i].K + 1) * nnf));
         PAT_CUDA(cudaMemcpyAsync(xf, ins[i].d_p0_io, ins[i].K * nnf * sizeof(float), cudaMemcpyDeviceToDevice, st));
         PAT_CUDA(cudaMemcpyAsync(xf + ins[i].K * nnf, ins[i].d_c_io, nnf * sizeof(float), cudaMemcpyDeviceToDevice,
