@@ -85,3 +85,40 @@ def test_reconstruct_configurations(L, B):
     assert L.pat_reconstruct_batched(ctypes.byref(_cfg(B)), 1, ctypes.byref(null_inst), None) == B.PAT_EINVAL
     assert L.pat_reconstruct(None, FAKE, FAKE, FAKE, FAKE, None, None) == B.PAT_EINVAL
     assert L.pat_reconstruct(ctypes.byref(_cfg(B, K=0)), FAKE, FAKE, FAKE, FAKE, None, None) == B.PAT_EINVAL
+
+
+def test_sensors_outside_the_grid_or_not_finite(L, B):
+    g = B.PatGrid(64, 22, 1e-4, 1e-8, 10, 1750.0, 1000.0, 2.0, 1500.0)
+    h = ctypes.c_void_p()
+    for x, y in ((-3.0e-3, 3e-3), (3e-3, 9.0e-3), (float("nan"), 3e-3), (3e-3, float("inf"))):
+        xy = (ctypes.c_double * 4)(3.2e-3, 3.2e-3, x, y)
+        assert L.pat_plan_create(ctypes.byref(h), ctypes.byref(g), 2, xy, 1, 32) == B.PAT_EINVAL, (x, y)
+        assert b"sensor 1" in L.pat_last_error() and not h.value
+    Ks = (ctypes.c_int * 2)(2, 0)
+    xy = (ctypes.c_double * 2)(3.2e-3, 3.2e-3)
+    assert L.pat_plan_create_batched(ctypes.byref(h), ctypes.byref(g), 1, xy, 2, Ks, 32) == B.PAT_EINVAL
+    assert b"instance 1" in L.pat_last_error()
+
+
+def _no_gpu():
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present: device allocations succeed")
+
+
+def test_failed_device_allocations_return_a_status_and_no_object(L, B):
+    """Without a device every allocation fails: each creator reports it and hands back nothing."""
+    _no_gpu()
+    g = B.PatGrid(64, 22, 1e-4, 1e-8, 10, 1750.0, 1000.0, 2.0, 1500.0)
+    xy = (ctypes.c_double * 2)(3.2e-3, 3.2e-3)
+    h = ctypes.c_void_p()
+    rc = L.pat_plan_create(ctypes.byref(h), ctypes.byref(g), 1, xy, 1, 32)
+    assert rc in (B.PAT_ENOMEM, B.PAT_ECUDA) and not h.value
+    assert b"CUDA error" in L.pat_last_error()
+    pr = ctypes.c_void_p()
+    rc = L.pat_prior_create(32, 1e-4, 1.5e-3, 2, ctypes.byref(pr))
+    assert rc in (B.PAT_ENOMEM, B.PAT_ECUDA) and not pr.value
+    net = ctypes.c_void_p()
+    rc = L.pat_unet_create(ctypes.byref(net), 2, 8, 1, 16, 16, 1)
+    assert rc in (B.PAT_ENOMEM, B.PAT_ECUDA) and not net.value
+    assert L.pat_last_error()
