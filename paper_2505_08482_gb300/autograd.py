@@ -23,16 +23,16 @@ class KSpaceForward(torch.autograd.Function):
         cc = c.detach().contiguous()
         ws = torch.empty(plan.workspace_bytes(B.PAT_WS_GRADIENT), dtype=torch.uint8, device=plan.device)
         y = plan.forward(cc, p0c, keep_checkpoints=True, ws=ws)
-        ctx.save_for_backward(p0c, cc)
+        # the workspace (checkpoints) is saved like the inputs: autograd releases it after the
+        # backward pass, or keeps it for another one when the graph is retained
+        ctx.save_for_backward(p0c, cc, ws)
         ctx.plan = plan
-        ctx.ws = ws
         return y
 
     @staticmethod
     def backward(ctx, ybar: torch.Tensor):
-        p0, c = ctx.saved_tensors
-        gp, gc = ctx.plan.vjp(c, p0, ybar.contiguous().to(torch.float32), ws=ctx.ws)
-        ctx.ws = None
+        p0, c, ws = ctx.saved_tensors
+        gp, gc = ctx.plan.vjp(c, p0, ybar.contiguous().to(torch.float32), ws=ws)
         return (gp if ctx.needs_input_grad[0] else None, gc if ctx.needs_input_grad[1] else None, None)
 
 
