@@ -200,17 +200,19 @@ int pat_forward_noalloc(pat_plan plan, const float* d_c, const float* d_p0, floa
  * d_w: device [K] float weights w_k = 1/sigma_k^2 (L_e^T L_e = w_k I).
  * d_J: device double[ninst] (may be NULL) receives J per instance.  d_y_pred: device
  * [K][nt][m] (may be NULL) receives the predicted traces.  The workspace
- * must hold PAT_WS_GRADIENT bytes.  Returns PAT_ENONFINITE only through
- * *d_flag semantics of pat_status (the call itself stays asynchronous). */
+ * must hold PAT_WS_GRADIENT bytes.  A NaN or Inf in J is reported by
+ * pat_status (PAT_STATUS_NONFINITE), not by the return value: the call
+ * stays asynchronous. */
 int pat_adjoint_grad(pat_plan plan, const float* d_c, const float* d_p0, const float* d_y_meas,
                      const float* d_w, float* d_grad_p0, float* d_grad_c, double* d_J,
                      float* d_y_pred, void* d_ws, size_t ws_bytes, void* stream);
 
 /* Vector-Jacobian product of the forward operator: given d_ybar [K][nt][m]
  * (the adjoint source, e.g. dL/dy), returns d_grad_p0 = (df/dp0)^T ybar and
- * d_grad_c = sum_k (df_k/dc)^T ybar_k.  Requires that the immediately
- * preceding pat_forward on this plan and workspace used the same d_c and
- * d_p0 with a PAT_WS_GRADIENT workspace (its checkpoints are reused). */
+ * d_grad_c = sum_k (df_k/dc)^T ybar_k.  Requires that d_ws holds the
+ * checkpoints of a pat_forward with the same d_c and d_p0 and a
+ * PAT_WS_GRADIENT workspace; calls in between that use other workspaces are
+ * allowed (the last segment's pressure history is then recomputed). */
 int pat_vjp(pat_plan plan, const float* d_c, const float* d_p0, const float* d_ybar,
             float* d_grad_p0, float* d_grad_c, void* d_ws, size_t ws_bytes, void* stream);
 
