@@ -41,3 +41,24 @@ def test_fullsize_traces_match_closed_form_samples(variant):
         den += np.sum(ex ** 2)
         assert np.abs(y[:, n] - ex).max() <= 1e-4 * np.abs(ex).max() + 1e-6 * np.abs(y).max()
     assert np.sqrt(num / den) <= 1e-4
+
+
+def test_fullsize_heterogeneous_traces_match_the_oracle_on_sampled_data_sets():
+    """The benchmark's grid, batch and kernel variant with its heterogeneous speed of sound:
+    traces are causal, so the first 300 samples of data sets 0 and 7 of the full run
+    (K = 8, Nt = 1800) equal an oracle run of 300 steps of that data set alone."""
+    from oracle import forward as F
+    from oracle.sensors import sensor_matrix
+    w = ps.workload("vessels256", 0)
+    plan = gpu_plan(grid_params(256, 1800), w.sensors, 8, ckpt_every=32)
+    plan.variant = 0
+    f = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float32, device="cuda")
+    y = plan.forward(f(w.c_true), f(w.p0_true)).cpu().numpy()
+    ns = 300
+    g = oracle_grid(grid_params(256, ns))
+    S = sensor_matrix(g, w.sensors)
+    for k in (0, 7):
+        ref = F.forward(g, w.c_true, w.p0_true[k:k + 1], S)[0]
+        assert np.abs(ref).max() > 0.1                     # the waves have reached the sensors
+        err = np.linalg.norm(y[k, :ns] - ref) / np.linalg.norm(ref)
+        assert err <= 1e-4, (k, err)
