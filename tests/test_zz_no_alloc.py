@@ -6,8 +6,9 @@ latency-critical loop that cannot afford the device synchronisation
 cudaMalloc may cause) create the plan ahead of time and then run the forward
 model with the library's static scratch array instead of a workspace.  The
 test calls it through the C ABI twice in a row and compares the traces with
-pat_forward's.  It lives in its own file, collected last, so a failure here
-stops a ``-x`` run only after every other test has run.
+pat_forward's.  It lives in its own file, collected after the other parity
+tests (only the slow full-size oracle comparisons follow it), so a failure here
+stops a ``-x`` run only after those have run.
 """
 import ctypes
 
