@@ -185,13 +185,22 @@ int pat_forward(pat_plan plan, const float* d_c, const float* d_p0, float* d_y,
  * PAT_NOALLOC_SCRATCH_BYTES (16 MiB) that every GPU loading the library
  * holds until exit.  Plans whose forward workspace
  * (pat_workspace_bytes(plan, PAT_WS_FORWARD)) exceeds it are rejected with
- * PAT_EINVAL and a message.  The plan's device must be current.  The first
- * call on a device looks up the array's device address (set-up), so make it
- * before any stream capture.  All calls share the array and it keeps the
- * last call's contents; calls that overlap on the GPU race on it.  No
- * checkpoints are kept, so it cannot precede pat_vjp. */
+ * PAT_EINVAL and a message.  The plan's device must be current.  The array's
+ * device address is looked up in the current context on every call (after a
+ * cudaDeviceReset it may move); the first call in a context loads the
+ * library's device code (set-up), so make it before any stream capture.  All
+ * calls share the array and it keeps the last call's contents; calls that
+ * overlap on the GPU (other streams, other threads, other plans) race on it.
+ * No checkpoints are kept, so it cannot precede pat_vjp. */
 #define PAT_NOALLOC_SCRATCH_BYTES (16 * 1024 * 1024)
 int pat_forward_noalloc(pat_plan plan, const float* d_c, const float* d_p0, float* d_y, void* stream);
+
+/* Status of the last pat_forward_noalloc with this plan, read from the
+ * static array after synchronising the stream: *h_flag gets PAT_STATUS_WAIT
+ * if a staged row pass (variant 3) gave up its bounded wait, so that the
+ * traces of that call are invalid; 0 otherwise.  The array is shared, so
+ * the answer concerns the last allocation-free call of any plan. */
+int pat_forward_noalloc_status(pat_plan plan, int* h_flag, void* stream);
 
 /* Data term and its gradient (Eq. Minimised_functional without priors;
  * Eqs. gradient_p0 and gradient_sos for the discrete scheme):

@@ -84,6 +84,7 @@ SIGNATURES = {
     "pat_workspace_bytes": (c_size_t, [c_void_p, c_int]),
     "pat_forward": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),
     "pat_forward_noalloc": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "pat_forward_noalloc_status": (c_int, [c_void_p, POINTER(c_int), c_void_p]),
     "pat_adjoint_grad": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                                  c_void_p, c_void_p, c_size_t, c_void_p]),
     "pat_vjp": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),

@@ -11,14 +11,15 @@
 // The scratch is the file-scope array below, PAT_NOALLOC_SCRATCH_BYTES
 // (16 MiB) per device: every GPU that loads this library holds it until the
 // process exits.  Host code cannot use the array's name as a device address
-// (on the host it names a stand-in object), so the first call on each device
-// looks the address up with cudaGetSymbolAddress while that device is
-// current and caches it; that first call should therefore come before any
-// stream capture.  All calls share the one array, which keeps the contents
-// of the last call; calls whose work overlaps on the GPU race on it.
+// (on the host it names a stand-in object), so every call looks the address
+// up with cudaGetSymbolAddress in the context that is current.  The address
+// is not cached: after cudaDeviceReset (or when the primary context is
+// released and created again) the module is loaded anew and the array may
+// sit elsewhere, and a cached address would then point at freed memory.  The
+// first call in a context loads the module (set-up); make it before any
+// stream capture.  All calls share the one array, which keeps the contents of
+// the last call; calls whose work overlaps on the GPU race on it.
 #include <cuda_runtime.h>
-
-#include <mutex>
 
 #include "pat_internal.h"
 
@@ -26,26 +27,23 @@ namespace {
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[PAT_NOALLOC_SCRATCH_BYTES];
 
-constexpr int kMaxDevices = 64;
-void* g_scratch_addr[kMaxDevices] = {};
-std::mutex g_scratch_mu;
-
-// Device address of g_noalloc_scratch on the current device (looked up once per device).
+// Device address of g_noalloc_scratch in the current context.
 int scratch_address(void** out) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return pat::cuda_fail(e, "cudaGetSymbolAddress(g_noalloc_scratch)");
+    *out = p;
+    return PAT_OK;
+}
+
+// The plan's device must be current.
+int check_device(const pat_plan_s* p, const char* who) {
     int dev = -1;
     PAT_CUDA(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= kMaxDevices) {
-        pat::set_error("pat_forward_noalloc: device index %d out of range", dev);
+    if (dev != p->device) {
+        pat::set_error("%s: the plan's device (%d) must be current, not %d", who, p->device, dev);
         return PAT_EINVAL;
     }
-    std::lock_guard<std::mutex> lock(g_scratch_mu);
-    if (!g_scratch_addr[dev]) {
-        void* p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess) return pat::cuda_fail(e, "cudaGetSymbolAddress(g_noalloc_scratch)");
-        g_scratch_addr[dev] = p;
-    }
-    *out = g_scratch_addr[dev];
     return PAT_OK;
 }
 
@@ -62,14 +60,10 @@ extern "C" int pat_forward_noalloc(pat_plan p, const float* c, const float* p0, 
                        p->ws_fwd, PAT_NOALLOC_SCRATCH_BYTES);
         return PAT_EINVAL;
     }
-    int dev = -1;
-    PAT_CUDA(cudaGetDevice(&dev));
-    if (dev != p->device) {
-        pat::set_error("pat_forward_noalloc: the plan's device (%d) must be current, not %d", p->device, dev);
-        return PAT_EINVAL;
-    }
+    int rc = check_device(p, "pat_forward_noalloc");
+    if (rc != PAT_OK) return rc;
     void* scratch = nullptr;
-    int rc = scratch_address(&scratch);
+    rc = scratch_address(&scratch);
     if (rc != PAT_OK) return rc;
     // the forward sweep writes every scratch region it reads before reading it,
     // so nothing left by an earlier call needs clearing
@@ -77,5 +71,26 @@ extern "C" int pat_forward_noalloc(pat_plan p, const float* c, const float* p0, 
     rc = pat::forward_sweep(p, c, p0, y, w, false, static_cast<cudaStream_t>(stream));
     if (rc != PAT_OK) return rc;
     p->hist_valid_ws = nullptr;
+    return PAT_OK;
+}
+
+// Status word of the last pat_forward_noalloc of this plan: the bounded-wait bit that the
+// staged row passes set in the scratch's flag region (the forward sets no other bit).
+extern "C" int pat_forward_noalloc_status(pat_plan p, int* h_flag, void* stream) {
+    if (!p || !h_flag) {
+        pat::set_error("pat_forward_noalloc_status: null argument");
+        return PAT_EINVAL;
+    }
+    int rc = check_device(p, "pat_forward_noalloc_status");
+    if (rc != PAT_OK) return rc;
+    void* scratch = nullptr;
+    rc = scratch_address(&scratch);
+    if (rc != PAT_OK) return rc;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int f[2] = {0, 0};
+    PAT_CUDA(cudaMemcpyAsync(f, static_cast<const char*>(scratch) + p->o_flag, 2 * sizeof(int),
+                             cudaMemcpyDeviceToHost, st));
+    PAT_CUDA(cudaStreamSynchronize(st));
+    *h_flag = f[1] ? PAT_STATUS_WAIT : 0;
     return PAT_OK;
 }

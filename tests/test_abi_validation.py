@@ -48,6 +48,16 @@ def test_null_plans_and_buffers(L, B):
         assert L.pat_last_error()
 
 
+def test_noalloc_null_arguments(L, B):
+    # each buffer NULL in turn (the plan pointer is never dereferenced: the checks come first)
+    for args in ((FAKE, None, FAKE, FAKE), (FAKE, FAKE, None, FAKE), (FAKE, FAKE, FAKE, None)):
+        assert L.pat_forward_noalloc(*args, None) == B.PAT_EINVAL
+        assert b"null argument" in L.pat_last_error()
+    flag = ctypes.c_int()
+    assert L.pat_forward_noalloc_status(None, ctypes.byref(flag), None) == B.PAT_EINVAL
+    assert L.pat_forward_noalloc_status(FAKE, None, None) == B.PAT_EINVAL
+
+
 def test_selftest_and_prior_arguments(L, B):
     assert L.pat_selftest_wait(None, 1000, None) == B.PAT_EINVAL
     assert L.pat_selftest_wait(FAKE, 0, None) == B.PAT_EINVAL
