@@ -363,6 +363,21 @@ typedef struct {
 int pat_reconstruct(const pat_recon_cfg* cfg, const float* d_y_meas, const float* d_w,
                     float* d_c_io, float* d_p0_io, pat_report* report, void* stream);
 
+/* The two transfers of the multigrid schedule, as pat_reconstruct applies
+ * them between levels (Sec. 3.1: the parameters of a converged level are
+ * interpolated to the next finer grid; Sec. 4.1.2: the data are interpolated
+ * linearly to each level's time grid).
+ * pat_prolong: bilinear resampling of nb fields d_src [nb][n_src][n_src] to
+ * d_dst [nb][n_dst][n_dst] on the cell-centred coordinates of the same
+ * physical square, constant beyond the outermost source cell centres.
+ * pat_time_interp: d_out [K][nt_dst][m] = linear interpolation in time of
+ * d_y [K][nt_src][m] (samples at n dt_src) at t = n dt_dst, held at the last
+ * sample beyond it.  Device buffers, asynchronous on the stream; PAT_EINVAL
+ * for a NULL buffer, a size < 1 or a time step that is not positive. */
+int pat_prolong(const float* d_src, float* d_dst, int nb, int n_src, int n_dst, void* stream);
+int pat_time_interp(const float* d_y, float* d_out, int K, int nt_src, int nt_dst, int m, double dt_src,
+                    double dt_dst, void* stream);
+
 /* ---- instrumentation (benchmarking; not thread-safe) ---- */
 
 /* Kernel classes that can be timed. */

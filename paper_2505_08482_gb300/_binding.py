@@ -100,6 +100,8 @@ SIGNATURES = {
     "pat_reconstruct": (c_int, [POINTER(PatReconCfg), c_void_p, c_void_p, c_void_p, c_void_p, POINTER(PatReport),
                                 c_void_p]),
     "pat_reconstruct_batched": (c_int, [POINTER(PatReconCfg), c_int, POINTER(PatInstance), c_void_p]),
+    "pat_prolong": (c_int, [c_void_p, c_void_p, c_int, c_int, c_int, c_void_p]),
+    "pat_time_interp": (c_int, [c_void_p, c_void_p, c_int, c_int, c_int, c_int, c_double, c_double, c_void_p]),
     "pat_plan_set_graphs": (c_int, [c_void_p, c_int]),
     "pat_plan_autotune": (c_int, [c_void_p, c_void_p, c_size_t, POINTER(c_double), c_void_p]),
     "pat_kernel_launches": (ctypes.c_ulonglong, []),

@@ -238,3 +238,22 @@ int vtime_interp(cudaStream_t st, const float* y, float* out, int K, int nts, in
 }
 
 }  // namespace pat
+
+// ---- C ABI of the two multigrid transfers (Sec. 3.1, Sec. 4.1.2) ----
+
+extern "C" int pat_prolong(const float* d_src, float* d_dst, int nb, int n_src, int n_dst, void* stream) {
+    if (!d_src || !d_dst || nb < 1 || n_src < 1 || n_dst < 1) {
+        pat::set_error("pat_prolong: null buffer or size < 1");
+        return PAT_EINVAL;
+    }
+    return pat::vresample(static_cast<cudaStream_t>(stream), d_src, d_dst, nb, n_src, n_dst);
+}
+
+extern "C" int pat_time_interp(const float* d_y, float* d_out, int K, int nt_src, int nt_dst, int m, double dt_src,
+                               double dt_dst, void* stream) {
+    if (!d_y || !d_out || K < 1 || nt_src < 1 || nt_dst < 1 || m < 1 || !(dt_src > 0.0) || !(dt_dst > 0.0)) {
+        pat::set_error("pat_time_interp: null buffer, size < 1 or time step not positive");
+        return PAT_EINVAL;
+    }
+    return pat::vtime_interp(static_cast<cudaStream_t>(stream), d_y, d_out, K, nt_src, nt_dst, m, dt_src, dt_dst);
+}

@@ -289,6 +289,31 @@ class Prior:
                                            _stream(stream)), "pat_prior_eval")
         return float(J.item()), grad, z, it.value
 
+def prolong(src, n_dst: int, stream=None):
+    """Bilinear prolongation of fields [nb][n][n] to [nb][n_dst][n_dst] (pat_prolong)."""
+    if src.dim() != 3 or src.shape[1] != src.shape[2]:
+        raise ValueError("src must be [nb][n][n]")
+    _f32(src, tuple(src.shape), "src", src.device)
+    out = torch.empty((src.shape[0], int(n_dst), int(n_dst)), dtype=torch.float32, device=src.device)
+    with torch.cuda.device(src.device):
+        B.check(B.lib().pat_prolong(_ptr(src), _ptr(out), int(src.shape[0]), int(src.shape[1]), int(n_dst),
+                                    _stream(stream)), "pat_prolong")
+    return out
+
+
+def time_interp(y, dt_src: float, dt_dst: float, nt_dst: int, stream=None):
+    """Linear interpolation of traces [K][nt][m] to t = n dt_dst, n < nt_dst (pat_time_interp)."""
+    if y.dim() != 3:
+        raise ValueError("y must be [K][nt][m]")
+    _f32(y, tuple(y.shape), "y", y.device)
+    K, nts, m = (int(v) for v in y.shape)
+    out = torch.empty((K, int(nt_dst), m), dtype=torch.float32, device=y.device)
+    with torch.cuda.device(y.device):
+        B.check(B.lib().pat_time_interp(_ptr(y), _ptr(out), K, nts, int(nt_dst), m, float(dt_src), float(dt_dst),
+                                        _stream(stream)), "pat_time_interp")
+    return out
+
+
 @dataclass
 class ReconConfig:
     """Parameters of pat_reconstruct (see include/pat.h)."""

@@ -58,6 +58,18 @@ def test_noalloc_null_arguments(L, B):
     assert L.pat_forward_noalloc_status(FAKE, None, None) == B.PAT_EINVAL
 
 
+def test_multigrid_transfer_arguments(L, B):
+    assert L.pat_prolong(None, FAKE, 1, 8, 16, None) == B.PAT_EINVAL
+    assert L.pat_prolong(FAKE, None, 1, 8, 16, None) == B.PAT_EINVAL
+    for nb, ns, nd in ((0, 8, 16), (1, 0, 16), (1, 8, 0)):
+        assert L.pat_prolong(FAKE, FAKE, nb, ns, nd, None) == B.PAT_EINVAL
+    assert L.pat_time_interp(None, FAKE, 1, 10, 20, 4, 1e-8, 5e-9, None) == B.PAT_EINVAL
+    for K, nts, ntd, m, dts, dtd in ((0, 10, 20, 4, 1e-8, 5e-9), (1, 10, 20, 0, 1e-8, 5e-9),
+                                     (1, 10, 20, 4, 0.0, 5e-9), (1, 10, 20, 4, 1e-8, float("nan"))):
+        assert L.pat_time_interp(FAKE, FAKE, K, nts, ntd, m, dts, dtd, None) == B.PAT_EINVAL
+    assert b"pat_time_interp" in L.pat_last_error()
+
+
 def test_selftest_and_prior_arguments(L, B):
     assert L.pat_selftest_wait(None, 1000, None) == B.PAT_EINVAL
     assert L.pat_selftest_wait(FAKE, 0, None) == B.PAT_EINVAL
