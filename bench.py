@@ -60,6 +60,12 @@ def bytes_per_cell(cls: int, ng: int, n: int, ckpt_hist: bool = True) -> float:
     return table[cls]
 
 
+# Algorithmic bytes per cell-step of a whole forward solve and of a gradient evaluation
+# (forward + segment recompute + adjoint), FP32: the state read and written once per step,
+# c, checkpoint amortisation, the stored history and the dJ/dc accumulation.
+FWD_BYTES = 36.5
+GRAD_BYTES = 125.0
+
 KERNEL_FILES = ("fft.cuh", "fft2l.cuh", "geo.cuh", "kfixed.cuh", "kfixed_300.cu", "kernels.cu", "api.cu")
 
 
@@ -82,6 +88,11 @@ def parse():
     ap.add_argument("--nt", type=int, default=WL["nt"], help="time samples (fewer only for profiling captures)")
     ap.add_argument("--no-graphs", action="store_true", help="launch every kernel from the host (no CUDA graphs)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-ttr", action="store_true", help="skip the time-to-relative-error comparison")
+    ap.add_argument("--ttr-instances", type=int, default=8)
+    ap.add_argument("--ttr-ec", type=float, default=2.0, help="E_c target (%%) of the time-to-target comparison")
+    ap.add_argument("--ttr-ep0", type=float, default=50.0, help="E_p0 target (%%) of the time-to-target comparison")
+    ap.add_argument("--ttr-iters", type=int, default=20)
     ap.add_argument("--variant", type=int, default=None,
                     help="use this kernel variant instead of the autotuner's choice (profiling runs)")
     ap.add_argument("--cpu-sample-steps", type=int, default=0, help="oracle sample length (0 = auto)")
@@ -209,8 +220,54 @@ def stored_traffic(cls: int, src_hash: str):
 
 
 # ---------------------------------------------------------------------------
-def oracle_sample(seed: int, nt_s: int, K_s: int = 1):
-    """One oracle gradient on a bounded sample of the workload; returns seconds."""
+def oracle_plain64():
+    """The oracle on the 64 x 64 plain workload (K = 1, M = 64, Nt = 400), timed whole on one core:
+    one forward, one gradient and one projected L-BFGS iteration from the plain start (seconds)."""
+    import numpy as np
+    import pat_synth as ps
+    from oracle.adjoint import adjoint_grad, objective
+    from oracle.forward import forward
+    from oracle.grid import make_grid
+    from oracle.lbfgs import projected_lbfgs
+    from oracle.sensors import sensor_matrix
+    w = ps.workload("plain64", 0)
+    g = make_grid(64, w.dx, 400, c_ref=WL["c_hi"], cfl=WL["cfl"])
+    S = sensor_matrix(g, w.sensors)
+    t0 = time.perf_counter()
+    y = forward(g, w.c_true, w.p0_true, S)
+    t1 = time.perf_counter()
+    ym = ps.add_noise(y, ps.rng_for(100))
+    wt = ps.noise_weights(ym)
+    c0 = np.full((64, 64), 0.5 * (w.c_true.min() + w.c_true.max()))
+    t2 = time.perf_counter()
+    adjoint_grad(g, c0, 0.5 * w.p0_true, S, ym, wt)
+    t3 = time.perf_counter()
+    npx = 64 * 64
+    unpack = lambda x: (x[:npx].reshape(1, 64, 64), x[npx:].reshape(64, 64))
+    fun = lambda x: objective(g, unpack(x)[1], unpack(x)[0], S, ym, wt)[0]
+
+    def fun_grad(x):
+        J, gp, gc = adjoint_grad(g, unpack(x)[1], unpack(x)[0], S, ym, wt)
+        return J, np.concatenate([gp.ravel(), gc.ravel()])
+
+    x0 = np.concatenate([np.zeros(npx), c0.ravel()])
+    lo = np.concatenate([np.zeros(npx), np.full(npx, WL["c_lo"])])
+    hi = np.concatenate([np.full(npx, np.inf), np.full(npx, WL["c_hi"])])
+    sc = np.concatenate([np.full(npx, 0.25), np.full(npx, (WL["c_hi"] - WL["c_lo"]) / 4.0)])
+    t4 = time.perf_counter()
+    projected_lbfgs(fun, fun_grad, x0, lo, hi, sc, mem=20, max_iter=1, rtol=0.0)
+    t5 = time.perf_counter()
+    return {"forward_s": t1 - t0, "gradient_s": t3 - t2, "lbfgs_iteration_s": t5 - t4, "cores": 1}
+
+
+def _oracle_pool_init():
+    import numpy  # noqa: F401
+    import oracle.adjoint  # noqa: F401
+
+
+def _oracle_grad_one(task):
+    """One oracle gradient of data set k of the headline workload over nt_s samples (seconds)."""
+    seed, k, nt_s = task
     import numpy as np
     import pat_synth as ps
     from oracle.adjoint import adjoint_grad
@@ -219,19 +276,85 @@ def oracle_sample(seed: int, nt_s: int, K_s: int = 1):
     w, c_init = inputs(seed)
     g = make_grid(w.n, w.dx, nt_s, c_ref=WL["c_hi"], cfl=WL["cfl"])
     S = sensor_matrix(g, w.sensors)
-    rng = ps.rng_for(1000 + seed)
-    ym = rng.standard_normal((K_s, nt_s, w.m)) * 0.01
-    p0 = 0.5 * w.p0_true[:K_s]
-    c0 = np.full((w.n, w.n), c_init)
+    ym = ps.rng_for(1000 + 16 * seed + k).standard_normal((1, nt_s, w.m)) * 0.01
     t = time.perf_counter()
-    adjoint_grad(g, c0, p0, S, ym, np.ones(K_s))
+    adjoint_grad(g, np.full((w.n, w.n), c_init), 0.5 * w.p0_true[k:k + 1], S, ym, np.ones(1))
     return time.perf_counter() - t
+
+
+class OraclePool:
+    """Spawned worker processes that run the oracle's gradient, one data set per task.
+
+    The K data sets of an evaluation are independent until their dJ/dc are summed, so the
+    oracle (single-threaded NumPy) runs them side by side, one process per host core.
+    """
+
+    def __init__(self, workers: int):
+        import multiprocessing as mp
+        from concurrent.futures import ProcessPoolExecutor
+        self.workers = workers
+        self.ex = ProcessPoolExecutor(workers, mp_context=mp.get_context("spawn"), initializer=_oracle_pool_init)
+        list(self.ex.map(time.sleep, [0.5] * workers))   # start every worker before timing
+
+    def sample(self, nt_s: int, K_s: int, seed: int = 0):
+        """Wall seconds of K_s one-data-set gradients run in parallel, and their summed CPU seconds."""
+        t = time.perf_counter()
+        per = list(self.ex.map(_oracle_grad_one, [(seed, k, nt_s) for k in range(K_s)]))
+        return time.perf_counter() - t, sum(per)
+
+    def close(self):
+        self.ex.shutdown()
+
+
+def cpu_workers() -> int:
+    return max(1, min(WL["K"], os.cpu_count() or 1))
 
 
 def cpu_value(seconds: float, nt_s: int, K_s: int) -> float:
     """Oracle grad evals/s scaled from a sample (cost is linear in K and in Nt)."""
     scale = (WL["K"] * (WL["nt"] - 1)) / float(K_s * (nt_s - 1))
     return 1.0 / (seconds * scale)
+
+
+def solo_class_times(plan, gs, sensors, c0, p0, stream, dev):
+    """Average launch time (us) of each kernel class with its launches timed alone.
+
+    Forward classes: every launch of the class bracketed by events in an eager forward sweep
+    (pat_forward on a forward workspace, nothing else on the GPU).  Adjoint classes: the same
+    in pat_vjp of a second plan that keeps the whole pressure history, whose reverse sweep
+    runs no recompute stream beside the adjoint.  Returns {(class, "forward"|"adjoint"):
+    (us per launch, launches timed)}.
+    """
+    import torch
+    from paper_2505_08482_gb300 import _binding as B
+    from paper_2505_08482_gb300.solver import Plan
+    L = B.lib()
+    K, nt, M = plan.K, plan.nt, plan.m
+    out = {}
+    y = torch.empty((K, nt, M), dtype=torch.float32, device=dev)
+    plan.forward(c0, p0, y=y, stream=stream)
+    for cls in (B.PAT_K_ROW_RHO, B.PAT_K_ROW_U, B.PAT_K_COL_GRAD, B.PAT_K_COL_PAIR):
+        B.check(L.pat_timing_enable(cls, 2 * nt, 1), "pat_timing_enable")
+        plan.forward(c0, p0, y=y, stream=stream)
+        tot, cnt = ctypes_read(L)
+        out[(cls, "forward")] = (1e3 * tot / max(cnt, 1), cnt)
+    B.check(L.pat_timing_enable(0, 0, 1), "pat_timing_enable")
+    hplan = Plan(gs, sensors, K, ckpt_every=nt, device=dev)
+    hplan.variant = plan.variant
+    ybar = torch.full((K, nt, M), 1e-3, dtype=torch.float32, device=dev)
+    for cls in (0, B.PAT_K_COL_PAIR, B.PAT_K_COL_SUM, B.PAT_K_ROW_ADJ_RHO, B.PAT_K_ROW_ADJ_U):
+        hplan.forward(c0, p0, y=y, keep_checkpoints=True, stream=stream)
+        if cls:
+            B.check(L.pat_timing_enable(cls, 2 * nt, 1), "pat_timing_enable")
+        hplan.vjp(c0, p0, ybar, stream=stream)
+        tot, cnt = ctypes_read(L)
+        if cls:
+            out[(cls, "adjoint")] = (1e3 * tot / max(cnt, 1), cnt)
+    B.check(L.pat_timing_enable(0, 0, 1), "pat_timing_enable")
+    torch.cuda.synchronize()
+    del hplan
+    torch.cuda.empty_cache()
+    return out
 
 
 def max_over_ranks(t_ms: float, device) -> float:
@@ -251,19 +374,30 @@ def whole_job_rate(world: int, steps: int, t_ms: float) -> float:
 def run_reference(args, rank):
     if rank != 0:
         return
-    nt_s = args.cpu_sample_steps or 300
+    nt_s = args.cpu_sample_steps or 200
+    pool = OraclePool(cpu_workers())
+    K = WL["K"]
     for _ in range(args.warmup):
-        oracle_sample(0, nt_s)
-    ts = [oracle_sample(0, nt_s) for _ in range(args.steps)]
-    t = sum(ts) / len(ts)
-    v = cpu_value(t, nt_s, 1)
+        pool.sample(nt_s, K)
+    walls, cpus = [], []
+    for _ in range(args.steps):
+        wall, cpu = pool.sample(nt_s, K)
+        walls.append(wall)
+        cpus.append(cpu)
+    pool.close()
+    t = sum(walls) / len(walls)
+    v = cpu_value(t, nt_s, K)
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 / v, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": cfg_dict(args),
-            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"one FP64 oracle gradient at K=1, Nt={nt_s} on the same 300^2 grid per "
-                                       f"step, scaled by K*(Nt-1) to K=8, Nt=1800"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": pool.workers, "kind": "oracle",
+                             "sample": f"per step: the FP64 oracle gradient of all K={K} data sets on the same "
+                                       f"300^2 grid over Nt={nt_s} samples, one data set per process on "
+                                       f"{pool.workers} host cores ({t:.2f} s wall), scaled by (Nt-1) to "
+                                       f"Nt={WL['nt']}; ms_per_step is that scaled time",
+                             "single_core_value": cpu_value(sum(cpus) / len(cpus), nt_s, K),
+                             "sample_wall_ms_per_step": 1000.0 * t, "nproc": os.cpu_count()},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -286,6 +420,8 @@ def run_ours(args, rank, world, local_rank):
     from paper_2505_08482_gb300.solver import GridSpec, Plan
 
     pkg.build()
+    # the oracle's worker processes start (spawn) before the first GPU call
+    pool = OraclePool(cpu_workers()) if (rank == 0 and world == 1 and not args.no_cpu_baseline) else None
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     L = B.lib()
@@ -325,25 +461,15 @@ def run_ours(args, rank, world, local_rank):
     for _ in range(args.warmup):
         grad_eval()
     torch.cuda.synchronize()
-    # per-class kernel time of one evaluation (outside the timed region) -> dominant kernel
-    per_class = {}
+    # launches of every kernel class in one evaluation (counted outside the timed region)
+    launches_per_eval = {}
     for cls in B.KERNEL_CLASSES:
         B.check(L.pat_timing_enable(cls, 8000, 1), "pat_timing_enable")
         grad_eval()
-        tot, cnt = ctypes_read(L)
-        per_class[cls] = (tot, cnt)
+        launches_per_eval[cls] = ctypes_read(L)[1]
     B.check(L.pat_timing_enable(0, 0, 1), "pat_timing_enable")
-    dom = max(per_class, key=lambda c: per_class[c][0])
-    per_eval_launches = per_class[dom][1]
-    # the dominant kernel's launch time: every 32nd launch (every launch of a segment kernel)
-    # bracketed by events, in eager mode (events inside a replayed graph are not per-launch
-    # timers); the timed region itself replays graphs unless --no-graphs
-    every = 32 if per_eval_launches > 1000 else 1
-    B.check(L.pat_timing_enable(dom, per_eval_launches * args.steps // every + 16, every), "pat_timing_enable")
-    for _ in range(args.steps):
-        grad_eval()
-    dom_ms, dom_cnt = ctypes_read(L)
-    B.check(L.pat_timing_enable(0, 0, 1), "pat_timing_enable")
+    torch.cuda.synchronize()
+    solo = solo_class_times(plan, gs, w.sensors, c0, p0, stream, dev)
     # the clock sampler starts here, so that its own start-up (NVML initialisation on a fresh
     # machine) falls before the timed region; it keeps only the samples inside the region
     sampler = ClockSampler(local_rank)
@@ -438,20 +564,41 @@ def run_ours(args, rank, world, local_rank):
         e2e_ms = max_over_ranks(e2e_ms, dev)
     e2e_val = whole_job_rate(world, args.steps, e2e_ms)
 
-    # roofline of the dominant kernel
+    # roofline of the dominant kernel: the class with the largest solo time per evaluation
+    # (solo launch time x launches per evaluation); its own launches timed alone
     peak, peak_kind = measured_peaks()
-    bpl = bytes_per_cell(dom, ng, n) * ng * ng * K
-    avg_s = dom_ms / 1000.0 / max(dom_cnt, 1)
-    achieved = bpl / avg_s / 1e9
     src_hash = kernel_source_hash()
-    roof = {"bound": "hbm", "kernel": B.KERNEL_CLASSES[dom], "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": achieved / peak, "traffic": stored_traffic(dom, src_hash),
-            "peak_kind": f"{peak_kind} hbm_gbs", "algorithmic_bytes_per_launch": bpl,
-            "avg_launch_us": avg_s * 1e6, "launches_timed": dom_cnt,
-            "sampling": f"every {every}{'nd' if every == 32 else 'st'} launch over --steps eager evaluations "
-                        "after the warm-up",
-            "share_of_step": (dom_ms / max(dom_cnt, 1)) * per_eval_launches / (t_ms / args.steps) if t_ms > 0 else None,
-            "per_class_ms_per_eval_unsampled": {B.KERNEL_CLASSES[c]: round(v[0], 3) for c, v in per_class.items()}}
+    # launches of each measured entry per evaluation: the forward classes run in the forward
+    # sweep and again in the segment recompute, the adjoint classes once
+    phase_launches = {k: (2 if k[1] == "forward" else 1) * (nt - 1) for k in solo}
+    dom_key = max(solo, key=lambda k: solo[k][0] * phase_launches[k])
+    dom, dom_phase = dom_key
+    dom_us, dom_cnt = solo[dom_key]
+    bpl = bytes_per_cell(dom, ng, n) * ng * ng * K
+    achieved = bpl / (dom_us * 1e-6) / 1e9
+    per_eval_ms = t_ms / args.steps
+    cells = ng * ng * K * (nt - 1)
+    roof = {"bound": "hbm", "kernel": f"{B.KERNEL_CLASSES[dom]} ({dom_phase} sweep)", "achieved": achieved,
+            "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": stored_traffic(dom, src_hash),
+            "peak_kind": f"{peak_kind} hbm_gbs (burst copy)", "algorithmic_bytes_per_launch": bpl,
+            "avg_launch_us": dom_us, "launches_timed": dom_cnt,
+            "timing": "every launch of the class bracketed by CUDA events on its stream in an eager sweep that "
+                      "runs alone on the GPU (forward classes: pat_forward; adjoint classes: pat_vjp of a plan "
+                      "that keeps the whole pressure history, so no recompute stream runs beside it); the events "
+                      "also end the programmatic launch overlap with the neighbouring kernels",
+            "solo_us_per_launch": {f"{B.KERNEL_CLASSES[c]} ({ph})": round(v[0], 3) for (c, ph), v in solo.items()},
+            "launches_per_eval": {B.KERNEL_CLASSES[c]: v for c, v in launches_per_eval.items()},
+            "share_of_eval_if_serialised": round(dom_us * 1e-3 * phase_launches[dom_key] / per_eval_ms, 3),
+            "note": "solo launch times are serialised times: inside an evaluation the passes overlap with their "
+                    "neighbours (programmatic dependent launch) and the recompute stream runs beside the "
+                    "adjoint, so solo time x launches summed over classes exceeds the evaluation time",
+            "step_level": {
+                "gradient": {"bytes_per_cell_step": GRAD_BYTES, "cell_steps": cells,
+                             "achieved_GBs": GRAD_BYTES * cells / (per_eval_ms * 1e-3) / 1e9,
+                             "frac": GRAD_BYTES * cells / (per_eval_ms * 1e-3) / 1e9 / peak},
+                "forward": {"bytes_per_cell_step": FWD_BYTES, "cell_steps": cells,
+                            "achieved_GBs": FWD_BYTES * cells / fwd_s / 1e9,
+                            "frac": FWD_BYTES * cells / fwd_s / 1e9 / peak}}}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
@@ -464,14 +611,90 @@ def run_ours(args, rank, world, local_rank):
             "autotune_ms_per_grad_eval": {str(v): round(t, 2) for v, t in tuned.items()}, "variant": plan.variant,
             "cuda_graphs": not args.no_graphs}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        nt_s = args.cpu_sample_steps or 300
-        ts = oracle_sample(0, nt_s)
-        v = cpu_value(ts, nt_s, 1)
-        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                                "sample": f"one FP64 oracle gradient at K=1, Nt={nt_s} on the same 300^2 grid "
-                                          f"({ts:.1f} s), scaled by K*(Nt-1) to K=8, Nt=1800"}
+        nt_s = args.cpu_sample_steps or 200
+        wall, cpu = pool.sample(nt_s, K)
+        pool.close()
+        v = cpu_value(wall, nt_s, K)
+        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": pool.workers, "kind": "oracle",
+                                "sample": f"the FP64 oracle gradient of all K={K} data sets on the same 300^2 grid "
+                                          f"over Nt={nt_s} samples, one data set per process on {pool.workers} "
+                                          f"host cores ({wall:.1f} s wall), scaled by (Nt-1) to Nt={WL['nt']}",
+                                "single_core_value": cpu_value(cpu, nt_s, K), "nproc": os.cpu_count(),
+                                "plain64_unscaled_s": oracle_plain64()}
+    if rank == 0 and world == 1 and not args.no_ttr:
+        line["time_to_rel_err"] = time_to_rel_err(args, dev)
     if rank == 0:
         print(json.dumps(line), flush=True)
+
+
+def time_to_rel_err(args, dev):
+    """Time to equal relative errors in c and p0 (Eq. RelativeError), plain GPU solve against the
+    batched solve, on the 128 x 128 vessel workload (K = 4, M = 256, Nt = 900, 6 inclusions,
+    levels 64 -> 128, 1 % noise).
+
+    Plain: the instances one after another, each a pat_reconstruct-equivalent call (one
+    instance).  Batched: all instances in one pat_reconstruct_batched call.  Every instance
+    stops once E_c <= ttr_ec and E_p0 <= ttr_ep0 on the finest level (at most ttr_iters L-BFGS
+    iterations per level).  All instances arrive at once: an instance's latency is the time
+    from the common start until its call returns.
+    """
+    import numpy as np
+    import torch
+
+    import pat_synth as ps
+    from paper_2505_08482_gb300.solver import GridSpec, Plan, ReconConfig, reconstruct_batched
+    f32 = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float32, device=dev)
+    n, K, M, nt = 128, 4, 256, 900
+    dx = WL["dx"]
+    gs = GridSpec(n=n, pml=pml_auto(n), dx=dx, dt=WL["cfl"] * dx / WL["c_hi"], nt=nt, c_ref=WL["c_hi"])
+    insts = []
+    for i in range(args.ttr_instances):
+        wl = ps.workload("vessels128", 7000 + i)
+        gen = Plan(gs, wl.sensors, K, device=dev)
+        y = ps.add_noise(gen.forward(f32(wl.c_true), f32(wl.p0_true)).cpu().numpy(), ps.rng_for(7500 + i))
+        del gen
+        insts.append(dict(y_meas=f32(y), w=f32(ps.noise_weights(y)),
+                          c_init=f32(np.full((n, n), 0.5 * (wl.c_true.min() + wl.c_true.max()))),
+                          c_true=f32(wl.c_true), p0_true=f32(wl.p0_true), ec_target=args.ttr_ec,
+                          ep0_target=args.ttr_ep0))
+    sensors = ps.workload("vessels128", 7000).sensors
+    cfg = ReconConfig(levels=(64, 128), L=n * dx, dt_data=gs.dt, nt_data=nt, sensors_xy=sensors, K=K,
+                      iters=args.ttr_iters, mem=20, ckpt_every=32, rtol=0.0)
+    reconstruct_batched(cfg, insts[:1])        # first use of the kernels of both levels
+    torch.cuda.synchronize()
+
+    def reached(rows):
+        fin = [r for r in rows if r["level"] == 1]
+        return bool(fin) and fin[-1]["Ec"] <= args.ttr_ec and fin[-1]["Ep0"] <= args.ttr_ep0
+
+    # plain: one instance per call, in arrival order
+    done, ok_plain, it_plain = [], [], []
+    t0 = time.perf_counter()
+    for ins in insts:
+        (res, _) = reconstruct_batched(cfg, [ins])
+        torch.cuda.synchronize()
+        done.append(time.perf_counter() - t0)
+        ok_plain.append(reached(res[0][2]))
+        it_plain.append(len(res[0][2]))
+    wall_plain = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    res, _ = reconstruct_batched(cfg, insts)
+    torch.cuda.synchronize()
+    wall_b = time.perf_counter() - t0
+    ok_b = [reached(r[2]) for r in res]
+    q = lambda v, f: float(np.percentile(v, f))
+    return {"workload": f"vessels128: 128x128, K={K}, M={M}, Nt={nt}, levels 64->128, "
+                        f"{args.ttr_instances} seeded instances arriving together",
+            "targets": {"E_c_pct": args.ttr_ec, "E_p0_pct": args.ttr_ep0,
+                        "max_iterations_per_level": args.ttr_iters},
+            "plain": {"wall_s": wall_plain, "latency_s_p50": q(done, 50), "latency_s_p99": q(done, 99),
+                      "reached": sum(ok_plain) / len(ok_plain),
+                      "iterations_median": float(np.median(it_plain))},
+            "batched": {"wall_s": wall_b, "latency_s_p50": wall_b, "latency_s_p99": wall_b,
+                        "reached": sum(ok_b) / len(ok_b),
+                        "iterations_median": float(np.median([len(r[2]) for r in res]))},
+            "speedup_batched_vs_plain": wall_plain / wall_b,
+            "warm_start": "bench.py --warmstart (trains the U-Net first: minutes)"}
 
 
 def run_batch(args):

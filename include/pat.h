@@ -342,6 +342,8 @@ typedef struct {
     double ms;      /* wall time of the iteration */
     double Ec;      /* E_c (%, Eq. RelativeError) after the step against the instance's
                        true c resampled to the level, or -1 without a true c */
+    double Ep0;     /* E_p0 (%, Eq. RelativeError over all K data sets stacked) after the
+                       step against the true p0 resampled to the level, or -1 without one */
 } pat_iter_report;
 
 typedef struct {
@@ -416,7 +418,10 @@ typedef struct {
     int K;
     pat_report* report;
     const float* d_c_true;   /* optional [N][N]: report E_c per iteration */
-    double ec_target;        /* > 0 with d_c_true: leave a level (the finest: stop) once E_c <= ec_target */
+    double ec_target;        /* > 0 with d_c_true: target of E_c */
+    const float* d_p0_true;  /* optional [K][N][N]: report E_p0 per iteration */
+    double ep0_target;       /* > 0 with d_p0_true: target of E_p0 */
+    /* an instance with targets leaves a level (the finest: stops) once it meets all of them */
 } pat_instance;
 
 /* Several independent reconstructions that share cfg (levels, domain,

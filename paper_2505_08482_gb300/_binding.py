@@ -57,7 +57,7 @@ class PatInstance(ctypes.Structure):
 
 class PatIterReport(ctypes.Structure):
     _fields_ = [("level", c_int), ("iter", c_int), ("J", c_double), ("gnorm", c_double), ("alpha", c_double),
-                ("trials", c_int), ("J_new", c_double), ("ms", c_double), ("Ec", c_double)]
+                ("trials", c_int), ("J_new", c_double), ("ms", c_double), ("Ec", c_double), ("Ep0", c_double)]
 
 
 class PatReport(ctypes.Structure):
@@ -67,7 +67,7 @@ class PatReport(ctypes.Structure):
 
 PatInstance._fields_ = [("d_y_meas", c_void_p), ("d_w", c_void_p), ("d_c_io", c_void_p), ("d_p0_io", c_void_p),
                         ("K", c_int), ("report", POINTER(PatReport)), ("d_c_true", c_void_p),
-                        ("ec_target", c_double)]
+                        ("ec_target", c_double), ("d_p0_true", c_void_p), ("ep0_target", c_double)]
 
 # name -> (restype, argtypes)
 SIGNATURES = {

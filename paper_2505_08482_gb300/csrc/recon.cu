@@ -44,13 +44,14 @@ using Clock = std::chrono::steady_clock;
 double ms_since(Clock::time_point t) { return std::chrono::duration<double, std::milli>(Clock::now() - t).count(); }
 
 // scalar slots per instance in the device scalar array
-enum { S_GD, S_DEC, S_GG, S_SY, S_SS, S_YY, S_MAX, S_BETA, S_H0, S_EC, S_CT, S_COUNT };
+enum { S_GD, S_DEC, S_GG, S_SY, S_SS, S_YY, S_MAX, S_BETA, S_H0, S_EC, S_CT, S_EP, S_PT, S_COUNT };
 
 struct Inst {
     int K;
     size_t V, n0;               // vector length, length of the p0 block
     float *x, *z, *g, *d, *xt, *zt, *gt, *q, *psi;
     float* ct = nullptr;        // true c resampled to the level (E_c tracking), or null
+    float* pt = nullptr;        // true p0 (all K) resampled to the level (E_p0 tracking), or null
     float* zp = nullptr;        // Xi^{-1} (x - eta) at the accepted point x (the prior solves' warm start)
     float* zpt = nullptr;       // the same at the trial point xt
     bool zp_warm = false;
@@ -291,6 +292,11 @@ int Batch::level(int li, const float* const* xprev, int nprev) {
             RC(vresample(st, ins[i].d_c_true, s.ct, 1, cfg.levels[cfg.nlevels - 1], N));
             RC(vdot(st, s.ct, s.ct, nn, sc(i, S_CT), part));
         }
+        if (ins[i].d_p0_true) {
+            RC(alloc(&s.pt, s.n0));
+            RC(vresample(st, ins[i].d_p0_true, s.pt, s.K, cfg.levels[cfg.nlevels - 1], N));
+            RC(vdot(st, s.pt, s.pt, s.n0, sc(i, S_PT), part));
+        }
     }
     RC(evaluate(true, false));
     for (int i = 0; i < ni; ++i) I[i].J = hJ[i];
@@ -392,7 +398,7 @@ int Batch::level(int li, const float* const* xprev, int nprev) {
             if (rep) {
                 if (rep->count < rep->capacity && rep->iters)
                     rep->iters[rep->count++] = pat_iter_report{
-                        li, it, s.J, std::sqrt(hs(i, S_GG)), 0.0, s.trials, s.J, ms_since(s.t_iter), -1.0};
+                        li, it, s.J, std::sqrt(hs(i, S_GG)), 0.0, s.trials, s.J, ms_since(s.t_iter), -1.0, -1.0};
                 rep->status = PAT_ELINESEARCH;
             }
             s.active = false;
@@ -420,6 +426,10 @@ int Batch::level(int li, const float* const* xprev, int nprev) {
                 RC(vaxpby(st, s.q, 1.f, s.xt + s.n0, -1.f, s.ct, nn));
                 RC(vdot(st, s.q, s.q, nn, sc(i, S_EC), part));
             }
+            if (s.pt) {   // E_p0 over all K data sets: || p0 - p0_true ||^2
+                RC(vaxpby(st, s.q, 1.f, s.xt, -1.f, s.pt, s.n0));
+                RC(vdot(st, s.q, s.q, s.n0, sc(i, S_EP), part));
+            }
         }
         RC(sync_scalars());
         for (int i : act) {
@@ -443,10 +453,11 @@ int Batch::level(int li, const float* const* xprev, int nprev) {
             }
             const double Jn = hJ[i];
             const double ec = s.ct ? 100.0 * std::sqrt(hs(i, S_EC) / hs(i, S_CT)) : -1.0;
+            const double ep = s.pt ? 100.0 * std::sqrt(hs(i, S_EP) / hs(i, S_PT)) : -1.0;
             pat_report* rep = ins[i].report;
             if (rep && rep->count < rep->capacity && rep->iters)
                 rep->iters[rep->count++] = pat_iter_report{li,      it, s.J, std::sqrt(hs(i, S_GG)), s.alpha,
-                                                           s.trials, Jn, ms_since(s.t_iter), ec};
+                                                           s.trials, Jn, ms_since(s.t_iter), ec, ep};
             const double rel = s.J > 0 ? (s.J - Jn) / s.J : 0.0;
             std::swap(s.z, s.zt);
             std::swap(s.x, s.xt);
@@ -454,8 +465,11 @@ int Batch::level(int li, const float* const* xprev, int nprev) {
             std::swap(s.zp, s.zpt);
             s.J = Jn;
             if (rel < cfg.rtol) s.active = false;
-            // a tracked instance leaves a level (the last one: stops) once E_c reaches its target
-            if (s.ct && ins[i].ec_target > 0 && ec <= ins[i].ec_target) s.active = false;
+            // a tracked instance leaves a level (the last one: stops) once every target it
+            // has (E_c, E_p0) is reached
+            const bool want_c = s.ct && ins[i].ec_target > 0, want_p = s.pt && ins[i].ep0_target > 0;
+            if ((want_c || want_p) && (!want_c || ec <= ins[i].ec_target) && (!want_p || ep <= ins[i].ep0_target))
+                s.active = false;
         }
     }
     return PAT_OK;
@@ -551,6 +565,6 @@ extern "C" int pat_reconstruct(const pat_recon_cfg* cfg, const float* y_meas, co
                                float* p0_io, pat_report* rep, void* stream) {
     if (!cfg || !y_meas || !w || !c_io || !p0_io) { set_error("pat_reconstruct: null argument"); return PAT_EINVAL; }
     if (cfg->K < 1) { set_error("pat_reconstruct: K < 1"); return PAT_EINVAL; }
-    pat_instance one{y_meas, w, c_io, p0_io, cfg->K, rep, nullptr, 0.0};
+    pat_instance one{y_meas, w, c_io, p0_io, cfg->K, rep, nullptr, 0.0, nullptr, 0.0};
     return pat_reconstruct_batched(cfg, 1, &one, stream);
 }

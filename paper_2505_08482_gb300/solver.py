@@ -361,7 +361,7 @@ def _cfg_struct(cfg: ReconConfig, K: int, xy):
 
 def _rows(rep, rows):
     return [dict(level=r.level, it=r.iter, J=r.J, gnorm=r.gnorm, alpha=r.alpha, trials=r.trials, J_new=r.J_new,
-                 ms=r.ms, Ec=r.Ec) for r in rows[:rep.count]]
+                 ms=r.ms, Ec=r.Ec, Ep0=r.Ep0) for r in rows[:rep.count]]
 
 
 def reconstruct_batched(cfg: ReconConfig, instances, stream=None, max_report=4096):
@@ -369,8 +369,9 @@ def reconstruct_batched(cfg: ReconConfig, instances, stream=None, max_report=409
 
     ``instances``: list of dicts with device tensors ``y_meas`` [K][nt][m],
     ``w`` [K], ``c_init`` [N][N] and optional ``p0_init`` [K][N][N], ``c_true``
-    [N][N] (E_c per iteration) and ``ec_target`` (leave a level, the finest:
-    stop, once E_c is reached).  Returns a list of (c, p0, report rows, status) and the
+    [N][N] (E_c per iteration), ``p0_true`` [K][N][N] (E_p0 per iteration) and
+    the targets ``ec_target`` / ``ep0_target`` (leave a level, the finest: stop,
+    once every given target is reached).  Returns a list of (c, p0, report rows, status) and the
     total wall time in ms.
     """
     N = int(cfg.levels[-1])
@@ -393,9 +394,13 @@ def reconstruct_batched(cfg: ReconConfig, instances, stream=None, max_report=409
         ct = ins.get("c_true")
         if ct is not None:
             _f32(ct, (N, N), "c_true", dev)
+        pt = ins.get("p0_true")
+        if pt is not None:
+            _f32(pt, (K, N, N), "p0_true", dev)
         structs.append(B.PatInstance(ym.data_ptr(), w.data_ptr(), c.data_ptr(), p0.data_ptr(), K,
                                      ctypes.pointer(rep), ct.data_ptr() if ct is not None else None,
-                                     float(ins.get("ec_target", 0.0))))
+                                     float(ins.get("ec_target", 0.0)), pt.data_ptr() if pt is not None else None,
+                                     float(ins.get("ep0_target", 0.0))))
         outs.append((c, p0))
     arr = (B.PatInstance * len(structs))(*structs)
     c_cfg, lv = _cfg_struct(cfg, 0, xy)

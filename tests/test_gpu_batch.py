@@ -159,3 +159,34 @@ def test_batched_reconstruction_equals_single_reconstructions(with_prior):
             assert (a["level"], a["it"], a["alpha"], a["trials"]) == (b["level"], b["it"], b["alpha"], b["trials"])
             assert a["J"] == b["J"] and a["J_new"] == b["J_new"]
         assert torch.equal(c_b, c_s) and torch.equal(p0_b, p0_s)
+
+
+def test_tracked_errors_and_joint_targets():
+    """E_c and E_p0 (Eq. RelativeError) reported per iteration equal the host's values at the
+    returned point, and an instance with both targets leaves a level once it meets both."""
+    from oracle.forward import forward
+    from oracle.metrics import relative_error
+    from oracle.sensors import sensor_matrix
+    from tests._problems import oracle_grid
+    from paper_2505_08482_gb300.solver import ReconConfig, reconstruct_batched
+    n = 64
+    xy = ps.circle_sensors(n, 32, 1e-4)
+    gp = grid_params(n, 200)
+    g = oracle_grid(gp)
+    S = sensor_matrix(g, xy)
+    (c, p0), = _instances(n, [2], 200, seed=11)
+    y = ps.add_noise(forward(g, c, p0, S), ps.rng_for(33))
+    base = dict(y_meas=_dev(y), w=_dev(ps.noise_weights(y)), c_init=_dev(np.full((n, n), 1510.0)),
+                c_true=_dev(c), p0_true=_dev(p0))
+    cfg = ReconConfig(levels=(32, 64), L=n * 1e-4, dt_data=g.dt, nt_data=g.nt, sensors_xy=xy, K=2, iters=4, mem=5)
+    (c_r, p0_r, rows, st), = reconstruct_batched(cfg, [base])[0]
+    last = rows[-1]
+    assert last["level"] == 1
+    assert abs(last["Ec"] - relative_error(c, c_r.cpu().numpy())) <= 1e-3 * last["Ec"]
+    ep_host = 100.0 * np.linalg.norm(p0_r.cpu().numpy() - p0) / np.linalg.norm(p0)
+    assert abs(last["Ep0"] - ep_host) <= 1e-3 * ep_host
+    # targets met at once: one iteration per level; a target for p0 alone that is never met: all iterations
+    (_, _, rows_easy, _), = reconstruct_batched(cfg, [dict(base, ec_target=1e3, ep0_target=1e3)])[0]
+    assert [r["level"] for r in rows_easy] == [0, 1]
+    (_, _, rows_hard, _), = reconstruct_batched(cfg, [dict(base, ec_target=1e3, ep0_target=1e-6)])[0]
+    assert len(rows_hard) == len(rows)

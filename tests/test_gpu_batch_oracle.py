@@ -22,14 +22,16 @@ def _dev(a):
     return torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float32, device="cuda")
 
 
-@pytest.mark.parametrize("n,Ks,nt", [(64, (1, 3, 8), 90), (256, (1, 2, 3), 40)])
+@pytest.mark.parametrize("n,Ks,nt", [(64, (1, 3, 8), 90), (256, (1, 2, 3), 60)])
 def test_batched_plan_matches_oracle_per_instance(n, Ks, nt):
     from oracle.adjoint import adjoint_grad
     from oracle.forward import forward
     from oracle.sensors import sensor_matrix
     rng = ps.rng_for(21)
     gp = grid_params(n, nt)
-    xy = ps.circle_sensors(n, 2 * n, 1e-4)
+    # sensors spread over the central region where the sources lie, so that every data set's
+    # waves reach many of them within the short time series
+    xy = ps.rng_for(22).uniform(0.25 * n, 0.75 * n, size=(2 * n, 2)) * 1e-4
     cs = [ps.ellipse_phantom(n, 3 + i, rng) for i in range(len(Ks))]
     p0s = [np.stack([ps.blob_p0(n, 4, rng, sigma_cells=(2.0, 4.0)) for _ in range(K)]) for K in Ks]
     plan = gpu_plan(gp, xy, list(Ks), ckpt_every=16)
