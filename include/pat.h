@@ -132,6 +132,20 @@ int pat_plan_variants(pat_plan plan);
 int pat_plan_set_variant(pat_plan plan, int variant);
 int pat_plan_variant(pat_plan plan);
 
+/* Persistent forward sweep (grid sides 108, 144, 180, 200, 240, 300): with
+ * enable != 0 every forward sweep of the plan (pat_forward, the forward part
+ * of pat_adjoint_grad, the objective evaluations of the reconstruction) is
+ * one launch instead of four per time step.  Its CTAs stay resident and take
+ * work items (pass, data set, tile) of all data sets of all instances from a
+ * counter in the workspace; an item waits only for its own data set's
+ * earlier passes, so data sets and instances advance independently.  Each
+ * wait is bounded: if one gives up (after 1 s) the status word gets
+ * PAT_STATUS_QUEUE (pat_status) and the results of that call are invalid.
+ * Same results as the launched passes.  PAT_EINVAL for other grid sides.
+ * pat_plan_persistent returns 1 if enabled, 0 if not, -1 for a NULL plan. */
+int pat_plan_set_persistent(pat_plan plan, int enable);
+int pat_plan_persistent(pat_plan plan);
+
 /* CUDA graphs: with enable != 0, the first pat_forward / pat_adjoint_grad
  * (or objective evaluation of pat_reconstruct) on a non-default stream with
  * a given set of buffers and kernel variant is captured into a CUDA graph and
@@ -229,9 +243,12 @@ int pat_vjp(pat_plan plan, const float* d_c, const float* d_p0, const float* d_y
  * stream: *h_flag bit 0 (PAT_STATUS_NONFINITE) if the last objective met a
  * NaN/Inf in J or a residual; bit 1 (PAT_STATUS_WAIT) if a kernel of the last
  * pat_forward / pat_adjoint_grad / pat_vjp gave up a bounded wait for its
- * staged copies (variant 3; the results of that call are then invalid). */
+ * staged copies (variant 3); bit 2 (PAT_STATUS_QUEUE) if a persistent sweep
+ * gave up waiting for a work item (the results of that call are then
+ * invalid in both cases). */
 #define PAT_STATUS_NONFINITE 1
 #define PAT_STATUS_WAIT 2
+#define PAT_STATUS_QUEUE 4
 
 /* Self-test of the bounded wait behind PAT_STATUS_WAIT: launches one CTA on
  * the stream whose threads wait for an mbarrier phase that never completes
@@ -240,6 +257,15 @@ int pat_vjp(pat_plan plan, const float* d_c, const float* d_p0, const float* d_y
  * *d_status.  No fault and no hang: the context stays usable.  PAT_EINVAL
  * for a NULL pointer or a timeout out of range. */
 int pat_selftest_wait(int* d_status, unsigned timeout_us, void* stream);
+
+/* Self-test of the bounded dependency wait behind PAT_STATUS_QUEUE: zeroes
+ * the device int[3] d_queue (ticket counter, abort flag, items done of one
+ * data set), then launches one CTA that waits for an item of that data set
+ * which nothing produces, gives up after timeout_us microseconds
+ * (1..1000000), ORs PAT_STATUS_QUEUE into *d_status and sets the abort flag
+ * d_queue[1].  No fault and no hang.  PAT_EINVAL for a NULL pointer or a
+ * timeout out of range. */
+int pat_selftest_queue(int* d_queue, int* d_status, unsigned timeout_us, void* stream);
 int pat_status(pat_plan plan, const void* d_ws, int* h_flag, void* stream);
 
 /* ---- Ornstein-Uhlenbeck prior (Eq. Minimised_functional, Sec. 4.1.2) ---- */

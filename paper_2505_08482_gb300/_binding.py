@@ -33,6 +33,7 @@ PAT_NOALLOC_SCRATCH_BYTES = 16 * 1024 * 1024
 PAT_WS_GRADIENT = 1
 PAT_STATUS_NONFINITE = 1
 PAT_STATUS_WAIT = 2
+PAT_STATUS_QUEUE = 4
 
 
 class PatGrid(ctypes.Structure):
@@ -90,6 +91,9 @@ SIGNATURES = {
     "pat_vjp": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),
     "pat_status": (c_int, [c_void_p, c_void_p, POINTER(c_int), c_void_p]),
     "pat_selftest_wait": (c_int, [c_void_p, ctypes.c_uint, c_void_p]),
+    "pat_selftest_queue": (c_int, [c_void_p, c_void_p, ctypes.c_uint, c_void_p]),
+    "pat_plan_set_persistent": (c_int, [c_void_p, c_int]),
+    "pat_plan_persistent": (c_int, [c_void_p]),
     "pat_prior_create": (c_int, [c_int, c_double, c_double, c_int, POINTER(c_void_p)]),
     "pat_prior_destroy": (c_int, [c_void_p]),
     "pat_prior_xi": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_void_p]),

@@ -64,6 +64,8 @@ int pat::forward_sweep(pat_plan_s* p, const float* c, const float* p0, float* y,
     PAT_CUDA(cudaMemsetAsync(w.flag + 1, 0, sizeof(int), st));   // bounded-wait status of this call
     const int last0 = (p->nseg - 1) * p->s_eff;
     float* hlast = keep ? hist_of(p, w, p->nseg - 1) : nullptr;
+    if (p->persistent && p->sweep)   // one launch: initial pass, every step, checkpoints, history
+        return launch_forward_persistent(L, w, p0, y, hlast, last0, keep ? w.ckpt : nullptr);
     RC(launch_row_rho(L, w, 1, p0, y, 0, (keep && last0 == 0) ? hlast : nullptr, 0));
     // segments of s steps with the state copied at their starts (one segment without checkpoints)
     const int seg = keep ? p->s_eff : p->nt;
@@ -170,8 +172,9 @@ template <class F>
 int with_graph(pat_plan_s* p, int kind, const std::array<const void*, 10>& key, size_t ws_bytes, cudaStream_t st,
                F&& body) {
     if (!p->use_graphs || st == nullptr) return body();
+    const int gv = 2 * p->variant + (p->persistent ? 1 : 0);   // kernel variant and sweep form
     for (auto& g : p->graphs)
-        if (g.kind == kind && g.variant == p->variant && g.key == key && g.ws_bytes == ws_bytes) {
+        if (g.kind == kind && g.variant == gv && g.key == key && g.ws_bytes == ws_bytes) {
             PAT_CUDA(cudaGraphLaunch(g.exec, st));
             add_launches(g.launches);
             g.last_use = ++p->graph_clock;
@@ -199,7 +202,7 @@ int with_graph(pat_plan_s* p, int kind, const std::array<const void*, 10>& key, 
     cudaGraphDestroy(graph);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
     const unsigned long long n = launches_so_far() - l0;
-    p->graphs.push_back(pat_plan_s::Graph{kind, p->variant, key, ws_bytes, exec, n, ++p->graph_clock});
+    p->graphs.push_back(pat_plan_s::Graph{kind, gv, key, ws_bytes, exec, n, ++p->graph_clock});
     PAT_CUDA(cudaGraphLaunch(exec, st));
     return PAT_OK;
 }
@@ -365,6 +368,6 @@ extern "C" int pat_status(pat_plan p, const void* ws, int* h_flag, void* stream)
     int f[2] = {0, 0};
     PAT_CUDA(cudaMemcpyAsync(f, b + p->o_flag, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
     PAT_CUDA(cudaStreamSynchronize(st));
-    *h_flag = (f[0] ? 1 : 0) | (f[1] ? 2 : 0);
+    *h_flag = (f[0] ? PAT_STATUS_NONFINITE : 0) | (f[1] & (PAT_STATUS_WAIT | PAT_STATUS_QUEUE));
     return PAT_OK;
 }

@@ -620,6 +620,45 @@ int launch_row_rho(const Launch& L, const Ws& w, int mode, const float* p0, floa
     return check_launch("k_row_rho");
 }
 
+int launch_forward_persistent(const Launch& L, const Ws& w, const float* p0, float* y, float* hist, int last0,
+                              float* ckpt) {
+    const pat_plan_s* p = L.p;
+    if (!p->sweep) {
+        set_error("no persistent sweep for grid side %d", p->ng);
+        return PAT_EINVAL;
+    }
+    const double nrm = double(p->ng) * p->ng;
+    SweepArgs a;
+    a.A = w.A;
+    a.B = w.B;
+    a.ux = w.ux;
+    a.uy = w.uy;
+    a.rx = w.rx;
+    a.ry = w.ry;
+    a.cg = w.cg;
+    a.p0 = p0;
+    a.y = y;
+    a.hist = hist;
+    a.last0 = last0;
+    a.ckpt = ckpt;
+    a.s = p->s_eff;
+    a.sg = float(p->g.dt / p->g.rho0 / nrm);
+    a.sd = float(p->g.dt * p->g.rho0 / nrm);
+    a.nsteps = p->nt - 1;
+    a.queue = w.queue;
+    a.wait_ns = kQueueWaitNs;
+    const Geo g = geo_ws(p, w);
+    if (double(p->sweep->items(g, a.nsteps)) >= 2147483647.0) {
+        set_error("persistent sweep: too many work items (K * nt too large)");
+        return PAT_EINVAL;
+    }
+    count_launch();
+    PAT_CUDA(cudaMemsetAsync(w.queue, 0, (size_t(p->K) + 2) * sizeof(int), L.st));
+    int rc = p->sweep->launch(g, L.st, a);
+    if (rc != PAT_OK) return rc;
+    return check_launch("kp_forward");
+}
+
 int launch_row_u(const Launch& L, const Ws& w, int init) {
     const pat_plan_s* p = L.p;
     prof_begin(PAT_K_ROW_U, L.st);

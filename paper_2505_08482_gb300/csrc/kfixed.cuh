@@ -24,6 +24,7 @@
 
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
 
 #include "fft2l.cuh"
@@ -98,6 +99,22 @@ __device__ __forceinline__ void mbar_wait(uint64_t* mb, uint32_t parity, int* st
 }
 
 // ---------------------------------------------------------------------------
+// Where a pass body runs.  A body computes one tile (bx) of one data set (k) and has two
+// dependency points: state_ready() before it fetches the state rows that the pass two
+// passes back wrote, input_ready() before it reads the spectra that the preceding pass
+// wrote.  A launched pass (one tile per CTA) relies on stream order for the first and
+// waits for the preceding kernel (programmatic dependent launch) at the second.  The
+// forward row passes can also copy the state rows they write into a checkpoint (ck_*);
+// a launched pass has no checkpoint target.
+struct LaunchedCtx {
+    int bx, k;
+    __device__ __forceinline__ void state_ready() const {}
+    __device__ __forceinline__ void input_ready() const { pdl_wait_then_release(); }
+    __device__ __forceinline__ float* ck_a() const { return nullptr; }
+    __device__ __forceinline__ float* ck_b() const { return nullptr; }
+};
+
+// ---------------------------------------------------------------------------
 // B layout of the packed inverse: b[k2] = Z[k1 + N1 k2] where Z is the full
 // spectrum of a + i b built from the half spectra rows ra (of a) and rb (of b).
 template <class F>
@@ -141,11 +158,11 @@ __device__ __forceinline__ void col_mults(const Geo& g, int kx, int ky, int op, 
 // The two fields (or the two outputs) of a column are handled by separate threads (f = 0, 1);
 // in mode 0 they share the first transform stage.
 // Tables and twiddles are staged before the dependency wait, the columns read after it.
-template <int N1, int N2, int CC>
-__global__ void __launch_bounds__(2 * CC * Fft2<N1, N2>::T) kf_col(Geo g, float2* __restrict__ A,
-                                                                  float2* __restrict__ B, int mode, int op,
-                                                                  float scale) {
+template <int N1, int N2, int CC, class Ctx>
+__device__ __forceinline__ void col_body(const Geo& g, const Ctx& ctx, float2* __restrict__ A,
+                                         float2* __restrict__ B, int mode, int op, float scale) {
     using F = Fft2<N1, N2>;
+    ctx.state_ready();
     constexpr int N = F::N;
     constexpr int NT = 2 * CC * F::T;
     extern __shared__ float2 sm[];
@@ -154,11 +171,11 @@ __global__ void __launch_bounds__(2 * CC * Fft2<N1, N2>::T) kf_col(Geo g, float2
     float2* MY = MX + N * CC;               // [N][CC]
     float2* Zf = MY + N * CC;               // forward transposes of the two threads' fields, [2][ZS][CC]
     float2* Zi = Zf + 2 * F::ZS * CC;       // inverse transposes of the two outputs, [2][ZS][CC]
-    const int k = blockIdx.y;
+    const int k = ctx.k;
     const int f = threadIdx.x / (CC * F::T);
     const int tl = threadIdx.x - f * (CC * F::T);
     const int c = tl % CC, idx = tl / CC;
-    const int kx = blockIdx.x * CC + c;
+    const int kx = ctx.bx * CC + c;
     const bool colok = kx < g.hc;
     const int kxc = colok ? kx : g.hc - 1;
     const size_t base = size_t(k) * N * g.hp + kxc;
@@ -170,14 +187,14 @@ __global__ void __launch_bounds__(2 * CC * Fft2<N1, N2>::T) kf_col(Geo g, float2
         const int i = decltype(I)::value * NT + threadIdx.x;
         if (i < N * CC) {
             const int cc = i % CC, ky = i / CC;
-            const int kxs = min(int(blockIdx.x) * CC + cc, g.hc - 1);
+            const int kxs = min(ctx.bx * CC + cc, g.hc - 1);
             float2 mx, my;
             col_mults(g, kxs, ky, op, scale, mx, my);
             MX[i] = mx;
             MY[i] = my;
         }
     });
-    pdl_wait_then_release();
+    ctx.input_ready();
     float2* Zmine = Zf + f * F::ZS * CC + c;
     // mode 0 has one input: the f = 1 threads read the f = 0 threads' first transform stage
     const bool own_fwd = mode != 0 || f == 0;
@@ -223,6 +240,13 @@ __global__ void __launch_bounds__(2 * CC * Fft2<N1, N2>::T) kf_col(Geo g, float2
             dst[base + size_t(idx + N2 * n1) * g.hp] = a[n1];
         });
     }
+}
+
+template <int N1, int N2, int CC>
+__global__ void __launch_bounds__(2 * CC * Fft2<N1, N2>::T) kf_col(Geo g, float2* __restrict__ A,
+                                                                  float2* __restrict__ B, int mode, int op,
+                                                                  float scale) {
+    col_body<N1, N2, CC>(g, LaunchedCtx{int(blockIdx.x), int(blockIdx.y)}, A, B, mode, op, scale);
 }
 
 // Split the natural-order spectra W[j] (of a_j + i b_j) of nseq rows into half spectra:
@@ -275,10 +299,10 @@ __device__ __forceinline__ uint32_t rows_bytes(int nr) {
 // velocity row pass; kind 0 forward: u <- a'(a' u - g) (init: u = g/2 first),
 // kind 1 adjoint: t' = a'(ub + g), ub <- a' t'.  Then (A, B) <- R2C of the new pair.
 // The state and PML factors are not written by the preceding kernel: fetched before the wait.
-template <int N1, int N2, int RR, bool STAGE>
-__global__ void __launch_bounds__(RR * Fft2<N1, N2>::T) kf_row_u(Geo g, float2* __restrict__ A,
-                                                                float2* __restrict__ B, float* __restrict__ ux,
-                                                                float* __restrict__ uy, int kind, int init) {
+template <int N1, int N2, int RR, bool STAGE, bool LATE, class Ctx>
+__device__ __forceinline__ void row_u_body(const Geo& g, const Ctx& ctx, float2* __restrict__ A,
+                                           float2* __restrict__ B, float* __restrict__ ux, float* __restrict__ uy,
+                                           int kind, int init) {
     using F = Fft2<N1, N2>;
     constexpr int N = F::N, T = F::T;
     extern __shared__ float2 sm[];
@@ -289,7 +313,7 @@ __global__ void __launch_bounds__(RR * Fft2<N1, N2>::T) kf_row_u(Geo g, float2* 
     float* Sy = Sx + RR * N;
     float* Sa = Sy + RR * N;                                           // PML factors [N]
     uint64_t* mb = reinterpret_cast<uint64_t*>(Sa + N);
-    const int k = blockIdx.y, y0 = blockIdx.x * RR;
+    const int k = ctx.k, y0 = ctx.bx * RR;
     const int r = threadIdx.x / T, idx = threadIdx.x % T;
     const int nr = min(RR, N - y0);
     const bool rowok = r < nr;
@@ -299,6 +323,7 @@ __global__ void __launch_bounds__(RR * Fft2<N1, N2>::T) kf_row_u(Geo g, float2* 
     float* uxr = ux + row * N;
     float* uyr = uy + row * N;
     const bool zero = kind == 0 && init;
+    ctx.state_ready();
     float sx[N1], sy[N1], fa[N1];
     if constexpr (STAGE) {
         if (threadIdx.x == 0) {
@@ -312,18 +337,18 @@ __global__ void __launch_bounds__(RR * Fft2<N1, N2>::T) kf_row_u(Geo g, float2* 
             }
             bulk_load(Sa, g.a_stag, N * sizeof(float), mb);
         }
-    } else if (aact) {
+    } else if (!LATE && aact) {
         static_for<0, N1>([&](auto I) {
             constexpr int n1 = decltype(I)::value;
             const int x = idx + N2 * n1;
-            sx[n1] = zero ? 0.f : uxr[x];
-            sy[n1] = zero ? 0.f : uyr[x];
+            sx[n1] = zero ? 0.f : __ldcg(uxr + x);
+            sy[n1] = zero ? 0.f : __ldcg(uyr + x);
             fa[n1] = g.a_stag[x];
         });
     }
     const float ay = g.a_stag[yy];
     for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = g.tw[i];
-    pdl_wait_then_release();
+    ctx.input_ready();
     float2 b[N2];
     if (bact) load_c2r_b<F>(b, idx, A + row * g.hp, B + row * g.hp);
     __syncthreads();
@@ -343,6 +368,10 @@ __global__ void __launch_bounds__(RR * Fft2<N1, N2>::T) kf_row_u(Geo g, float2* 
                 ax = Sa[x];
                 ux0 = zero ? 0.f : Sx[r * N + x];
                 uy0 = zero ? 0.f : Sy[r * N + x];
+            } else if constexpr (LATE) {   // fetched where used (fewer registers)
+                ax = g.a_stag[x];
+                ux0 = zero ? 0.f : __ldcg(uxr + x);
+                uy0 = zero ? 0.f : __ldcg(uyr + x);
             } else {
                 ax = fa[n1];
                 ux0 = sx[n1];
@@ -355,6 +384,11 @@ __global__ void __launch_bounds__(RR * Fft2<N1, N2>::T) kf_row_u(Geo g, float2* 
                 const float uyn = ay * (ay * uyo - gv.y);
                 uxr[x] = uxn;
                 uyr[x] = uyn;
+                if (float* ck = ctx.ck_a()) {   // checkpoint copy of u^{n+1/2} (rows of data set k)
+                    const size_t o = row * N + x;
+                    ck[o] = uxn;
+                    ck[o + size_t(g.K) * N * N] = uyn;
+                }
                 a[n1] = make_float2(uxn, uyn);
             } else {
                 const float tpx = ax * (ux0 + gv.x);
@@ -372,17 +406,22 @@ __global__ void __launch_bounds__(RR * Fft2<N1, N2>::T) kf_row_u(Geo g, float2* 
                    [&](int j) { return B + (size_t(k) * N + y0 + j) * g.hp; });
 }
 
+template <int N1, int N2, int RR, bool STAGE>
+__global__ void __launch_bounds__(RR * Fft2<N1, N2>::T) kf_row_u(Geo g, float2* __restrict__ A,
+                                                                float2* __restrict__ B, float* __restrict__ ux,
+                                                                float* __restrict__ uy, int kind, int init) {
+    row_u_body<N1, N2, RR, STAGE, false>(g, LaunchedCtx{int(blockIdx.x), int(blockIdx.y)}, A, B, ux, uy, kind, init);
+}
+
 // density / pressure row pass (mode 0 regular, 1 init from p0, 2 restore), sensor gather,
 // history, then A <- R2C of p (two rows per complex transform).  State, medium and PML are
 // written two or more kernels earlier: fetched before the wait.
-template <int N1, int N2, int RR, bool STAGE>
-__global__ void __launch_bounds__(RR * Fft2<N1, N2>::T) kf_row_rho(Geo g, float2* __restrict__ A,
-                                                                  const float2* __restrict__ B,
-                                                                  float* __restrict__ rx, float* __restrict__ ry,
-                                                                  const float* __restrict__ cg, int mode,
-                                                                  const float* __restrict__ p0,
-                                                                  float* __restrict__ y, int tstep,
-                                                                  float* __restrict__ hist, int hist_slot) {
+template <int N1, int N2, int RR, bool STAGE, bool LATE, class Ctx>
+__device__ __forceinline__ void row_rho_body(const Geo& g, const Ctx& ctx, float2* __restrict__ A,
+                                             const float2* __restrict__ B, float* __restrict__ rx,
+                                             float* __restrict__ ry, const float* __restrict__ cg, int mode,
+                                             const float* __restrict__ p0, float* __restrict__ y, int tstep,
+                                             float* __restrict__ hist, int hist_slot) {
     using F = Fft2<N1, N2>;
     constexpr int N = F::N, T = F::T;
     extern __shared__ float2 sm[];
@@ -395,7 +434,7 @@ __global__ void __launch_bounds__(RR * Fft2<N1, N2>::T) kf_row_rho(Geo g, float2
     float* Sc = Sy + RR * N;
     float* Sa = Sc + RR * N;                                // PML factors [N]
     uint64_t* mb = reinterpret_cast<uint64_t*>(Sa + N);
-    const int k = blockIdx.y, y0 = blockIdx.x * RR;
+    const int k = ctx.k, y0 = ctx.bx * RR;
     const int r = threadIdx.x / T, idx = threadIdx.x % T;
     const int nr = min(RR, N - y0);
     const bool rowok = r < nr;
@@ -412,6 +451,7 @@ __global__ void __launch_bounds__(RR * Fft2<N1, N2>::T) kf_row_rho(Geo g, float2
         return (xd >= 0 && xd < g.n && yd >= 0 && yd < g.n) ? p0[(size_t(k) * g.n + yd) * g.n + xd] : 0.f;
     };
     float s0[N1], s1[N1], cc[N1], fa[N1];
+    ctx.state_ready();
     if constexpr (STAGE) {
         if (threadIdx.x == 0) {
             const size_t r0 = (size_t(k) * N + y0) * N;
@@ -425,19 +465,19 @@ __global__ void __launch_bounds__(RR * Fft2<N1, N2>::T) kf_row_rho(Geo g, float2
             bulk_load(Sc, medium_of(g, cg, k) + size_t(y0) * N, bytes, mb);
             bulk_load(Sa, g.a_cell, N * sizeof(float), mb);
         }
-    } else if (aact) {
+    } else if (!LATE && aact) {
         static_for<0, N1>([&](auto I) {
             constexpr int n1 = decltype(I)::value;
             const int x = idx + N2 * n1;
             cc[n1] = cr[x];
             fa[n1] = g.a_cell[x];
-            s0[n1] = mode == 1 ? p0_at(x) : rxr[x];
-            s1[n1] = mode == 1 ? 0.f : ryr[x];
+            s0[n1] = mode == 1 ? p0_at(x) : __ldcg(rxr + x);
+            s1[n1] = mode == 1 ? 0.f : __ldcg(ryr + x);
         });
     }
     const float acy = g.a_cell[yy];
     for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = g.tw[i];
-    pdl_wait_then_release();
+    ctx.input_ready();
     float2 b[N2];
     if (bact) load_c2r_b<F>(b, idx, A + row * g.hp, B + row * g.hp);
     __syncthreads();
@@ -461,6 +501,11 @@ __global__ void __launch_bounds__(RR * Fft2<N1, N2>::T) kf_row_rho(Geo g, float2
                 acx = Sa[x];
                 v0 = mode == 1 ? p0_at(x) : Sx[r * N + x];
                 v1 = mode == 1 ? 0.f : Sy[r * N + x];
+            } else if constexpr (LATE) {   // fetched where used (fewer registers)
+                c = cr[x];
+                acx = g.a_cell[x];
+                v0 = mode == 1 ? p0_at(x) : __ldcg(rxr + x);
+                v1 = mode == 1 ? 0.f : __ldcg(ryr + x);
             } else {
                 c = cc[n1];
                 acx = fa[n1];
@@ -474,6 +519,11 @@ __global__ void __launch_bounds__(RR * Fft2<N1, N2>::T) kf_row_rho(Geo g, float2
                 const float ryn = acy * (acy * v1 - gv.y);
                 rxr[x] = rxn;
                 ryr[x] = ryn;
+                if (float* ck = ctx.ck_b()) {   // checkpoint copy of rho^{n+1} (rows of data set k)
+                    const size_t o = row * N + x;
+                    ck[o] = rxn;
+                    ck[o + size_t(g.K) * N * N] = ryn;
+                }
                 pv = c * c * (rxn + ryn);
             } else if (mode == 1) {
                 pv = v0;
@@ -514,6 +564,18 @@ __global__ void __launch_bounds__(RR * Fft2<N1, N2>::T) kf_row_rho(Geo g, float2
     finish_fwd<F>(Z1 + r * F::ZS, idx, pairok && idx < N1);
     unpack_rows<F>(Z1, np, [&](int j) { return A + (size_t(k) * N + y0 + 2 * j) * g.hp; },
                    [&](int j) { return A + (size_t(k) * N + y0 + 2 * j + 1) * g.hp; });
+}
+
+template <int N1, int N2, int RR, bool STAGE>
+__global__ void __launch_bounds__(RR * Fft2<N1, N2>::T) kf_row_rho(Geo g, float2* __restrict__ A,
+                                                                  const float2* __restrict__ B,
+                                                                  float* __restrict__ rx, float* __restrict__ ry,
+                                                                  const float* __restrict__ cg, int mode,
+                                                                  const float* __restrict__ p0,
+                                                                  float* __restrict__ y, int tstep,
+                                                                  float* __restrict__ hist, int hist_slot) {
+    row_rho_body<N1, N2, RR, STAGE, false>(g, LaunchedCtx{int(blockIdx.x), int(blockIdx.y)}, A, B, rx, ry, cg, mode, p0,
+                                    y, tstep, hist, hist_slot);
 }
 
 // adjoint density row pass: pb = C2R(Q) + S^T r^n; rb += c^2 pb; cbar += 2 p pb / c;
@@ -699,6 +761,7 @@ inline void launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t sme
 template <int N1, int N2, int RR, int CC, bool STAGE>
 struct FixedImpl {
     using F = Fft2<N1, N2>;
+    static constexpr int n1 = N1, n2 = N2, rr = RR, cc = CC;
     using RS = RowSmem<F, RR>;
     static constexpr size_t smem_col = (F::N + 2 * F::N * CC + 4 * F::ZS * CC) * sizeof(float2);
     static_assert(2 * F::ZS >= F::ZS + F::N1 * F::N2, "product hand-off fits the inverse buffer");
@@ -770,5 +833,208 @@ struct MixedImpl {
         return FixedOps{C::F::N, 0, 0, &configure, &C::col, &U::row_u, &R::row_rho, &J::row_adj_rho, &CS::col};
     }
 };
+
+
+// ---------------------------------------------------------------------------
+// Persistent forward sweep: one launch runs the initial pass and all Nt-1 steps of every
+// data set of the plan (all instances of a batch).  The passes of the sweep are cut into
+// work items (pass q, data set k, tile b), numbered pass by pass and, within a pass, data
+// set by data set; CTAs take item numbers from a counter in the workspace (a ticket queue)
+// and run the same pass bodies as the launched passes.  An item waits only for the items
+// of its own data set in the passes before it (a per-data-set counter of completed items),
+// so data sets advance independently and a pass of one data set overlaps the tail of
+// another's.  Every item a CTA waits for has a smaller number and was taken earlier by a
+// running CTA, and the smallest unfinished item never waits, so the sweep progresses
+// whatever the number of resident CTAs.  Each wait is bounded: after kQueueWaitNs it sets
+// PAT_STATUS_QUEUE in the workspace status word and an abort flag that ends every later
+// wait at once (the results of that sweep are then invalid; no hang).
+struct SweepArgs {
+    float2* A;
+    float2* B;
+    float *ux, *uy, *rx, *ry;   // state [K][ng][ng] each (contiguous, ux first)
+    const float* cg;            // c on the grid [ninst][ng][ng]
+    const float* p0;            // [K][n][n]
+    float* y;                   // traces [K][nt][m], zeroed
+    float* hist;                // pressure history of the last segment (levels >= last0), or null
+    int last0;
+    float* ckpt;                // checkpoints [slot][4][K][ng][ng] at levels j s (slot j-1), or null
+    int s;
+    float sg, sd;               // scales of the G and D multipliers
+    int nsteps;                 // Nt - 1
+    int* queue;                 // [0] ticket counter, [1] abort flag, [2 + k] items done of data set k
+    unsigned long long wait_ns; // limit of one dependency wait
+};
+
+constexpr unsigned long long kQueueWaitNs = 1000000000ull;
+constexpr int kStatusQueue = 4;   // PAT_STATUS_QUEUE
+
+struct QueueCtx {
+    int bx, k;
+    int need_state, need_input;   // items of data set k that must be done at each dependency point
+    int* queue;
+    int* status;
+    float* cka;                   // checkpoint targets of the velocity / density rows, or null
+    float* ckb;
+    unsigned long long wait_ns;
+    __device__ __forceinline__ void wait(int need) const {
+        if (threadIdx.x == 0) {
+            const volatile int* done = queue + 2 + k;
+            const volatile int* abort_flag = queue + 1;
+            if (*done < need && !*abort_flag) {
+                const uint64_t t0 = global_ns();
+                while (*done < need && !*abort_flag) {
+                    if (global_ns() - t0 > wait_ns) {
+                        if (status) atomicOr(status, kStatusQueue);
+                        atomicExch(queue + 1, 1);
+                        break;
+                    }
+                    __nanosleep(64);
+                }
+            }
+            __threadfence();
+        }
+        __syncthreads();
+    }
+    __device__ __forceinline__ void state_ready() const { wait(need_state); }
+    __device__ __forceinline__ void input_ready() const { wait(need_input); }
+    __device__ __forceinline__ float* ck_a() const { return cka; }
+    __device__ __forceinline__ float* ck_b() const { return ckb; }
+};
+
+// C: column passes, U: velocity row passes, R: density row passes (one thread count)
+template <class C, class U, class R>
+struct PersistentImpl {
+    static constexpr int N = C::F::N;
+    static constexpr int NT = 2 * C::cc * C::F::T;
+    static_assert(U::F::N == N && R::F::N == N, "one grid side");
+    static_assert(U::rr * U::F::T == NT && R::rr * R::F::T == NT && U::rr == R::rr, "one thread count");
+    static constexpr int RR = U::rr, CC = C::cc;
+    static constexpr int MINB = 2;   // CTAs per SM the register budget is cut for
+    static constexpr size_t smem = C::smem_col > U::smem_u ? (C::smem_col > R::smem_rho ? C::smem_col : R::smem_rho)
+                                                           : (U::smem_u > R::smem_rho ? U::smem_u : R::smem_rho);
+    static int blocks_per_sm;
+
+    // The row bodies fetch the state where they use it (LATE): other CTAs of the sweep hide
+    // that latency.  The bodies are outlined (each its own register allocation): inlined
+    // into one item loop, values shared across them stay live at once and spill.
+    static __device__ __noinline__ void init_pass(const Geo& g, const QueueCtx& ctx, const SweepArgs& a) {
+        row_rho_body<R::n1, R::n2, RR, false, true>(g, ctx, a.A, a.B, a.rx, a.ry, a.cg, 1, a.p0, a.y, 0,
+                                              (a.hist && a.last0 == 0) ? a.hist : nullptr, 0);
+    }
+    static __device__ __noinline__ void col_pass(const Geo& g, const QueueCtx& ctx, const SweepArgs& a, int op) {
+        col_body<C::n1, C::n2, CC>(g, ctx, a.A, a.B, op, op, op ? a.sd : a.sg);
+    }
+    static __device__ __noinline__ void u_pass(const Geo& g, const QueueCtx& ctx, const SweepArgs& a, int init) {
+        row_u_body<U::n1, U::n2, RR, false, true>(g, ctx, a.A, a.B, a.ux, a.uy, 0, init);
+    }
+    static __device__ __noinline__ void rho_pass(const Geo& g, const QueueCtx& ctx, const SweepArgs& a, int lv) {
+        const bool h = a.hist && lv >= a.last0;
+        row_rho_body<R::n1, R::n2, RR, false, true>(g, ctx, a.A, a.B, a.rx, a.ry, a.cg, 0, nullptr, a.y, lv,
+                                              h ? a.hist : nullptr, lv - a.last0);
+    }
+
+    static __device__ __forceinline__ void run(const Geo& g, const SweepArgs& a) {
+        const int K = g.K;
+        const int nbc = (g.hc + CC - 1) / CC, nbr = (N + RR - 1) / RR;
+        const int per_k_step = 2 * nbc + 2 * nbr;
+        const int per_step = K * per_k_step;
+        const int total = K * nbr + per_step * a.nsteps;
+        const size_t f = size_t(K) * N * N;
+        __shared__ int s_item;
+        for (;;) {
+            __syncthreads();   // the previous item is finished with shared memory and s_item
+            if (threadIdx.x == 0) s_item = atomicAdd(a.queue, 1);
+            __syncthreads();
+            const int item = s_item;
+            if (item >= total) return;
+            QueueCtx ctx{0, 0, 0, 0, a.queue, g.status, nullptr, nullptr, a.wait_ns};
+            if (item < K * nbr) {   // initial condition from p0
+                ctx.k = item / nbr;
+                ctx.bx = item - ctx.k * nbr;
+                init_pass(g, ctx, a);
+            } else {
+                const int i2 = item - K * nbr;
+                const int n = i2 / per_step;
+                int r = i2 - n * per_step;
+                int p, pre, prev;
+                if (r < K * nbc) {
+                    p = 0; pre = 0; prev = nbr;
+                    ctx.k = r / nbc; ctx.bx = r - ctx.k * nbc;
+                } else if ((r -= K * nbc) < K * nbr) {
+                    p = 1; pre = nbc; prev = nbc;
+                    ctx.k = r / nbr; ctx.bx = r - ctx.k * nbr;
+                } else if ((r -= K * nbr) < K * nbc) {
+                    p = 2; pre = nbc + nbr; prev = nbr;
+                    ctx.k = r / nbc; ctx.bx = r - ctx.k * nbc;
+                } else {
+                    r -= K * nbc;
+                    p = 3; pre = 2 * nbc + nbr; prev = nbc;
+                    ctx.k = r / nbr; ctx.bx = r - ctx.k * nbr;
+                }
+                ctx.need_input = nbr + n * per_k_step + pre;
+                ctx.need_state = ctx.need_input - prev;
+                const int lv = n + 1;   // level written by this step
+                float* ck = (a.ckpt && lv % a.s == 0) ? a.ckpt + size_t(lv / a.s - 1) * 4 * f : nullptr;
+                if (p == 0 || p == 2) {
+                    col_pass(g, ctx, a, p == 2 ? 1 : 0);
+                } else if (p == 1) {
+                    ctx.cka = ck;
+                    u_pass(g, ctx, a, n == 0 ? 1 : 0);
+                } else {
+                    ctx.ckb = ck ? ck + 2 * f : nullptr;
+                    rho_pass(g, ctx, a, lv);
+                }
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                __threadfence();
+                atomicAdd(a.queue + 2 + ctx.k, 1);
+            }
+        }
+    }
+};
+
+template <class C, class U, class R>
+int PersistentImpl<C, U, R>::blocks_per_sm = 0;
+
+template <class P>
+__global__ void __launch_bounds__(P::NT, P::MINB) kp_forward(Geo g, SweepArgs a) {
+    P::run(g, a);
+}
+
+// launch table of the persistent sweep of one grid side
+struct SweepOps {
+    int ng;
+    int (*configure)();
+    int (*launch)(const Geo&, cudaStream_t, const SweepArgs&);
+    int (*items)(const Geo&, int nsteps);
+};
+
+template <class P>
+struct SweepImpl {
+    static int configure() {
+        cudaError_t e = cudaFuncSetAttribute((const void*)kp_forward<P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             int(P::smem));
+        if (e == cudaSuccess && P::blocks_per_sm == 0)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&P::blocks_per_sm, kp_forward<P>, P::NT, P::smem);
+        if (e == cudaSuccess && P::blocks_per_sm < 1) return cuda_fail(cudaErrorInvalidConfiguration, "kp_forward");
+        return e == cudaSuccess ? PAT_OK : cuda_fail(e, "cudaFuncSetAttribute(kp_forward)");
+    }
+    static int items(const Geo& g, int nsteps) {
+        const int nbc = (g.hc + P::CC - 1) / P::CC, nbr = (P::N + P::RR - 1) / P::RR;
+        return g.K * nbr + g.K * (2 * nbc + 2 * nbr) * nsteps;
+    }
+    static int launch(const Geo& g, cudaStream_t st, const SweepArgs& a) {
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        const int grid = std::max(1, std::min(items(g, a.nsteps), P::blocks_per_sm * std::max(sms, 1)));
+        kp_forward<P><<<grid, P::NT, P::smem, st>>>(g, a);
+        return PAT_OK;
+    }
+    static SweepOps ops() { return SweepOps{P::N, &configure, &launch, &items}; }
+};
+
+const SweepOps* sweep_ops_for(int ng);   // nullptr if the side has no persistent sweep
 
 }  // namespace pat

@@ -13,11 +13,18 @@ using A8 = FixedImpl<16, 15, 8, 2, false>;
 using S4 = FixedImpl<16, 15, 4, 4, true>;
 using B4 = FixedImpl<15, 16, 4, 4, false>;
 using C8 = FixedImpl<16, 15, 4, 8, false>;
+using PA = FixedImpl<16, 15, 8, 4, false>;   // persistent sweep: columns and velocity rows
+using PB = FixedImpl<15, 16, 8, 4, false>;   // persistent sweep: density rows
 }  // namespace
 
 const FixedOps* fixed_ops_240(int v) {
     static const FixedOps ops[] = {MixedImpl<A4, A4, B4, B4, C8>::ops(), A4::ops(), A8::ops(), S4::ops(), B4::ops()};
     return (v >= 0 && v < 5) ? &ops[v] : nullptr;
+}
+
+const SweepOps* sweep_ops_240() {
+    static const SweepOps ops = SweepImpl<PersistentImpl<PA, PA, PB>>::ops();
+    return &ops;
 }
 
 }  // namespace pat

@@ -91,6 +91,6 @@ extern "C" int pat_forward_noalloc_status(pat_plan p, int* h_flag, void* stream)
     PAT_CUDA(cudaMemcpyAsync(f, static_cast<const char*>(scratch) + p->o_flag, 2 * sizeof(int),
                              cudaMemcpyDeviceToHost, st));
     PAT_CUDA(cudaStreamSynchronize(st));
-    *h_flag = f[1] ? PAT_STATUS_WAIT : 0;
+    *h_flag = f[1] & (PAT_STATUS_WAIT | PAT_STATUS_QUEUE);
     return PAT_OK;
 }

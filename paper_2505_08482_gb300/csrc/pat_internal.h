@@ -15,6 +15,7 @@
 namespace pat {
 
 struct FixedOps;
+struct SweepOps;
 void set_error(const char* fmt, ...);
 int cuda_fail(cudaError_t e, const char* where);
 
@@ -45,6 +46,7 @@ struct Ws {
     float* cg;                                    // c on the grid [ninst][ng][ng]
     float2* A; float2* B;                         // spectra [K][ng][hc]
     double* J; double* part; int* flag;           // objective per instance, partial sums [K][32], flag
+    int* queue;                                   // persistent sweep: tickets, abort flag, done per data set
     // gradient only
     float* ckpt;                                  // [nseg-1][4][K][ng][ng]
     float* hist;                                  // [2][K][s_eff][ng][ng] pressure history (two segments)
@@ -66,6 +68,8 @@ struct pat_plan_s {
     int ninst;         // instances sharing the grid; K counts the data sets of all of them
     pat::FftDesc fft;
     const pat::FixedOps* fast;   // fixed-size passes for this grid side (nullptr: generic Stockham)
+    const pat::SweepOps* sweep;  // persistent forward sweep of this grid side (nullptr: none)
+    bool persistent;             // forward sweeps run as one persistent launch
     int variant;       // -1 generic, else index of the fixed-size tile variant
     int R;             // rows per CTA in row passes (even)
     int C;             // spectral columns per CTA in column passes
@@ -75,7 +79,7 @@ struct pat_plan_s {
     int nent;
     size_t ws_fwd, ws_grad;
     // layout offsets (bytes)
-    size_t o_state, o_cg, o_A, o_B, o_J, o_part, o_flag;
+    size_t o_state, o_cg, o_A, o_B, o_J, o_part, o_flag, o_queue;
     size_t o_ckpt, o_hist, o_adj, o_A2, o_B2, o_cbar, o_resid, o_ypred;
     // host bookkeeping: the workspace whose history holds the last segment
     const void* hist_valid_ws;
@@ -133,6 +137,10 @@ int launch_medium(const Launch& L, const float* c_dom, float* cg);
 int launch_row_rho(const Launch& L, const Ws& w, int mode, const float* p0, float* y, int tstep,
                    float* hist, int hist_slot);
 int launch_row_u(const Launch& L, const Ws& w, int init);
+// the whole forward sweep (initial pass and nt-1 steps) as one persistent launch; checkpoints
+// every s steps into ckpt (null: none), pressure history of levels >= last0 into hist (null: none)
+int launch_forward_persistent(const Launch& L, const Ws& w, const float* p0, float* y, float* hist, int last0,
+                              float* ckpt);
 // column passes: mode 0 = one input (A) -> (MX A, MY A) into (A, B)
 //                mode 1 = (A, B) -> (MX A, MY B); mode 2 = (A, B) -> MX A + MY B into A
 // op 0: G multipliers, op 1: D multipliers

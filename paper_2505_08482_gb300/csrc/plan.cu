@@ -83,6 +83,7 @@ Ws resolve(const pat_plan_s* p, void* base, bool grad) {
     w.J = reinterpret_cast<double*>(b + p->o_J);
     w.part = reinterpret_cast<double*>(b + p->o_part);
     w.flag = reinterpret_cast<int*>(b + p->o_flag);
+    w.queue = reinterpret_cast<int*>(b + p->o_queue);
     if (grad) {
         w.ckpt = reinterpret_cast<float*>(b + p->o_ckpt);
         w.hist = reinterpret_cast<float*>(b + p->o_hist);
@@ -111,6 +112,7 @@ static void layout(pat_plan_s* p) {
     p->o_J = o; o = align256(o + size_t(p->ninst) * sizeof(double));
     p->o_part = o; o = align256(o + size_t(p->K) * kResidBlocks * sizeof(double));
     p->o_flag = o; o = align256(o + 4 * sizeof(int));
+    p->o_queue = o; o = align256(o + (size_t(p->K) + 2) * sizeof(int));
     p->ws_fwd = o;
     p->o_ckpt = o; o = align256(o + size_t(std::max(p->nseg - 1, 0)) * 4 * f);
     p->o_hist = o; o = align256(o + size_t(p->nseg > 1 ? 2 : 1) * p->K * p->s_eff * p->ng * p->ng * sizeof(float));
@@ -158,6 +160,27 @@ extern "C" int pat_plan_set_variant(pat_plan plan, int variant) {
 }
 
 extern "C" int pat_plan_variant(pat_plan plan) { return plan ? plan->variant : -2; }
+
+extern "C" int pat_plan_set_persistent(pat_plan plan, int enable) {
+    if (!plan) { set_error("pat_plan_set_persistent: null plan"); return PAT_EINVAL; }
+    if (!enable) {
+        plan->persistent = false;
+        return PAT_OK;
+    }
+    const SweepOps* so = sweep_ops_for(plan->ng);
+    if (!so) {
+        set_error("pat_plan_set_persistent: grid side %d has no persistent sweep (sides 108, 144, 180, 200, 240, 300)",
+                  plan->ng);
+        return PAT_EINVAL;
+    }
+    int rc = so->configure();
+    if (rc != PAT_OK) return rc;
+    plan->sweep = so;
+    plan->persistent = true;
+    return PAT_OK;
+}
+
+extern "C" int pat_plan_persistent(pat_plan plan) { return plan ? int(plan->persistent) : -1; }
 
 extern "C" int pat_plan_set_graphs(pat_plan plan, int enable) {
     if (!plan) { set_error("pat_plan_set_graphs: null plan"); return PAT_EINVAL; }
@@ -215,6 +238,8 @@ extern "C" int pat_plan_create_batched(pat_plan* out, const pat_grid* g, int m, 
     p->s_eff = std::min(ckpt_every, g->nt);
     p->nseg = (g->nt + p->s_eff - 1) / p->s_eff;
     p->hist_valid_ws = nullptr;
+    p->sweep = nullptr;
+    p->persistent = false;
     p->use_graphs = false;
     p->graph_clock = 0;
     p->side = nullptr;

@@ -189,6 +189,16 @@ class Plan:
                                 self.workspace_bytes(B.PAT_WS_GRADIENT), _stream(stream)), "pat_vjp")
         return gp, gc
 
+    @property
+    def persistent(self) -> bool:
+        """Forward sweeps as one persistent launch (pat_plan_set_persistent)."""
+        return bool(B.lib().pat_plan_persistent(self._h) == 1)
+
+    @persistent.setter
+    def persistent(self, enable: bool):
+        with torch.cuda.device(self.device):
+            B.check(B.lib().pat_plan_set_persistent(self._h, int(bool(enable))), "pat_plan_set_persistent")
+
     def set_graphs(self, enable: bool = True):
         """Capture whole calls into CUDA graphs and replay them (pat_plan_set_graphs)."""
         B.check(B.lib().pat_plan_set_graphs(self._h, int(bool(enable))), "pat_plan_set_graphs")

@@ -71,6 +71,11 @@ def test_multigrid_transfer_arguments(L, B):
 
 
 def test_selftest_and_prior_arguments(L, B):
+    assert L.pat_plan_set_persistent(None, 1) == B.PAT_EINVAL
+    assert L.pat_plan_persistent(None) == -1
+    assert L.pat_selftest_queue(None, FAKE, 1000, None) == B.PAT_EINVAL
+    assert L.pat_selftest_queue(FAKE, None, 1000, None) == B.PAT_EINVAL
+    assert L.pat_selftest_queue(FAKE, FAKE, 0, None) == B.PAT_EINVAL
     assert L.pat_selftest_wait(None, 1000, None) == B.PAT_EINVAL
     assert L.pat_selftest_wait(FAKE, 0, None) == B.PAT_EINVAL
     assert L.pat_selftest_wait(FAKE, 2000000, None) == B.PAT_EINVAL
