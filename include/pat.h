@@ -495,6 +495,31 @@ int pat_unet_grads(pat_unet net, const float* d_in, const float* d_target, int B
 int pat_unet_train_step(pat_unet net, const float* d_in, const float* d_target, int B, float lr, double* d_loss,
                         void* stream);
 
+/* Tensor-core path of the network's GEMMs: 0 (default) the warp-level BF16
+ * MMA (mma.sync m16n8k16, operands staged by cp.async); 1 the fifth-generation
+ * tensor cores: tcgen05.mma (kind::f16, BF16 operands, FP32 accumulator in
+ * tensor memory) on 128 x 128 tiles whose 128 x 64 operand blocks are copied
+ * by TMA (cp.async.bulk.tensor, 128-byte swizzle) into a 4-stage ring of
+ * shared memory; GEMMs whose operands the TMA cannot address (K < 64,
+ * pitches not multiples of 8, unaligned bases) keep the warp-level path.
+ * Every wait of the tcgen05 kernel is bounded: if one gives up, the network's
+ * status word gets PAT_STATUS_TC05 (pat_unet_status; the results of that
+ * call are invalid). */
+#define PAT_STATUS_TC05 8
+int pat_unet_set_gemm_path(pat_unet net, int path);
+int pat_unet_status(pat_unet net, int* h_flag, void* stream);
+
+/* The network's BF16 GEMM on its own, for tests and measurement:
+ * d_C[M][N] (FP32, row pitch ldc) = d_A[M][K] . d_B[N][K]^T with BF16
+ * operands in row-major storage (row pitches lda, ldb in elements), FP32
+ * accumulation.  path 0: warp-level MMA (K, lda, ldb multiples of 8);
+ * path 1: tcgen05 (K >= 64, lda and ldb multiples of 8, 16-byte aligned
+ * operands; PAT_EINVAL otherwise).  d_status (device int, may be NULL) gets
+ * PAT_STATUS_TC05 if a bounded wait of the tcgen05 kernel gave up.
+ * Asynchronous on the stream. */
+int pat_gemm_bf16(const void* d_A, int lda, const void* d_B, int ldb, int M, int N, int K, float* d_C, int ldc,
+                  int path, int* d_status, void* stream);
+
 /* Message describing the last error on the calling thread. */
 const char* pat_last_error(void);
 

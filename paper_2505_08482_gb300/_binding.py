@@ -34,6 +34,7 @@ PAT_WS_GRADIENT = 1
 PAT_STATUS_NONFINITE = 1
 PAT_STATUS_WAIT = 2
 PAT_STATUS_QUEUE = 4
+PAT_STATUS_TC05 = 8
 
 
 class PatGrid(ctypes.Structure):
@@ -120,6 +121,10 @@ SIGNATURES = {
     "pat_unet_forward": (c_int, [c_void_p, c_void_p, c_int, c_void_p, c_void_p]),
     "pat_unet_grads": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_void_p, c_void_p, c_void_p]),
     "pat_unet_train_step": (c_int, [c_void_p, c_void_p, c_void_p, c_int, ctypes.c_float, c_void_p, c_void_p]),
+    "pat_unet_set_gemm_path": (c_int, [c_void_p, c_int]),
+    "pat_unet_status": (c_int, [c_void_p, POINTER(c_int), c_void_p]),
+    "pat_gemm_bf16": (c_int, [c_void_p, c_int, c_void_p, c_int, c_int, c_int, c_int, c_void_p, c_int, c_int, c_void_p,
+                              c_void_p]),
     "pat_last_error": (c_char_p, []),
 }
 

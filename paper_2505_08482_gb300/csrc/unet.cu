@@ -69,6 +69,8 @@ struct pat_unet_s {
     long long step = 0;
     std::vector<void*> allocs;
     int device = 0;
+    int gemm_path = 0;                   // 0 warp-level tensor cores (mma.sync), 1 tcgen05 / TMEM / TMA
+    int* status = nullptr;               // device status word of the tcgen05 GEMMs (PAT_STATUS_TC05)
 };
 
 namespace {
@@ -83,6 +85,14 @@ int dalloc(pat_unet_s* u, T** p, size_t n) {
     return PAT_OK;
 }
 
+// one GEMM of the network on the selected tensor-core path (tcgen05 where its operands allow)
+int net_gemm(pat_unet_s* u, cudaStream_t st, const __nv_bfloat16* A, int lda, const __nv_bfloat16* B, int ldb, int M,
+             int N, int K, const float* bias, int relu, void* C, int ldc, int out_mode, int splitk) {
+    if (u->gemm_path == 1 && unet_gemm_tc05_supported(A, lda, B, ldb, M, N, K))
+        return unet_gemm_tc05(st, A, lda, B, ldb, M, N, K, bias, relu, C, ldc, out_mode, splitk, u->status);
+    return unet_gemm(st, A, lda, B, ldb, M, N, K, bias, relu, C, ldc, out_mode, splitk);
+}
+
 // conv forward: out = ReLU(conv(in) + b) (relu=0 for the final 1x1)
 int conv_fwd(pat_unet_s* u, cudaStream_t st, const Conv& c, const __nv_bfloat16* in, int ldin, int B, void* out,
              int out_mode, int relu) {
@@ -91,10 +101,10 @@ int conv_fwd(pat_unet_s* u, cudaStream_t st, const Conv& c, const __nv_bfloat16*
     const float* bias = u->param + c.b_off;
     if (c.k == 3) {
         RC(unet_im2col(st, in, u->col, B, c.H, c.W, c.cin, ldin, 0));
-        return unet_gemm(st, u->col, 9 * c.cin, wb, 9 * c.cin, P, c.cout, 9 * c.cin, bias, relu, out, c.cout,
+        return net_gemm(u, st, u->col, 9 * c.cin, wb, 9 * c.cin, P, c.cout, 9 * c.cin, bias, relu, out, c.cout,
                          out_mode, 1);
     }
-    return unet_gemm(st, in, ldin, wb, c.cin, P, c.cout, c.cin, bias, relu, out, c.cout, out_mode, 1);
+    return net_gemm(u, st, in, ldin, wb, c.cin, P, c.cout, c.cin, bias, relu, out, c.cout, out_mode, 1);
 }
 
 // conv backward: given dz = dL/d(pre-activation) [P][cout], accumulate the parameter gradients
@@ -116,13 +126,13 @@ int conv_bwd(pat_unet_s* u, cudaStream_t st, const Conv& c, const __nv_bfloat16*
     }
     PAT_CUDA(cudaMemsetAsync(dW, 0, c.nw() * sizeof(float), st));
     const int splitk = std::max(1, std::min(64, P / 4096));
-    RC(unet_gemm(st, u->dt, P, u->colt, P, c.cout, K1, P, nullptr, 0, dW, K1, 2, splitk));
+    RC(net_gemm(u, st, u->dt, P, u->colt, P, c.cout, K1, P, nullptr, 0, dW, K1, 2, splitk));
     if (!din) return PAT_OK;
     // data gradient: din[p][ci] = sum_{tap,co} dz[p - off(tap)][co] W[co][tap][ci]
     if (c.k == 3) {
         RC(unet_weight_t(st, u->wbf + c.wb_off, u->wt, c.cout, c.cin));
         RC(unet_im2col(st, dz, u->col, B, c.H, c.W, c.cout, c.cout, 1));
-        return unet_gemm(st, u->col, 9 * c.cout, u->wt, 9 * c.cout, P, c.cin, 9 * c.cout, nullptr, 0, din, c.cin,
+        return net_gemm(u, st, u->col, 9 * c.cout, u->wt, 9 * c.cout, P, c.cin, 9 * c.cout, nullptr, 0, din, c.cin,
                          0, 1);
     }
     return PAT_EINVAL;
@@ -287,6 +297,8 @@ extern "C" int pat_unet_create(pat_unet* out, int levels, int base, int in_ch, i
     if (rc == PAT_OK) rc = dalloc(u, &u->out, size_t(max_batch) * H * W);
     if (rc == PAT_OK) rc = dalloc(u, &u->part, 256);
     if (rc == PAT_OK) rc = dalloc(u, &u->loss, 1);
+    if (rc == PAT_OK) rc = dalloc(u, &u->status, 1);
+    if (rc == PAT_OK && cudaMemset(u->status, 0, sizeof(int)) != cudaSuccess) rc = cuda_fail(cudaGetLastError(), "unet status");
     if (rc != PAT_OK) {
         pat_unet_destroy(u);
         return rc;
@@ -377,13 +389,13 @@ static int loss_and_grads(pat_unet_s* u, cudaStream_t st, const float* d_in, con
     {
         const int splitk = std::max(1, std::min(64, int(P / 4096)));
         // rows 1..7 of the transposed output gradient are zero; only row 0 (= dW) is kept
-        RC(unet_gemm(st, u->dt, int(P), u->col, int(P), 1, c.cin, int(P), nullptr, 0, dW, c.cin, 2, splitk));
+        RC(net_gemm(u, st, u->dt, int(P), u->col, int(P), 1, c.cin, int(P), nullptr, 0, dW, c.cin, 2, splitk));
     }
     // data gradient of the final conv: dtop[p][ci] = dout[p] W[ci]: GEMM with K = 8 (W padded)
     __nv_bfloat16* wpad = u->wt;
     PAT_CUDA(cudaMemsetAsync(wpad, 0, size_t(c.cin) * 8 * sizeof(__nv_bfloat16), st));
     RC(unet_copy_ch(st, u->wbf + c.wb_off, wpad, size_t(c.cin), 1, 1, 8, 0));
-    RC(unet_gemm(st, doutc, 8, wpad, 8, int(P), c.cin, 8, nullptr, 0, top.g, c.cin, 0, 1));
+    RC(net_gemm(u, st, doutc, 8, wpad, 8, int(P), c.cin, 8, nullptr, 0, top.g, c.cin, 0, 1));
     // the rest of the network
     Layout L = layout_of(u);
     auto& A = u->acts;
@@ -445,4 +457,40 @@ extern "C" int pat_unet_train_step(pat_unet u, const float* d_in, const float* d
     RC(sync_bf16(u, st));
     if (d_loss) PAT_CUDA(cudaMemcpyAsync(d_loss, u->loss, sizeof(double), cudaMemcpyDeviceToDevice, st));
     return PAT_OK;
+}
+
+extern "C" int pat_unet_set_gemm_path(pat_unet u, int path) {
+    if (!u || path < 0 || path > 1) { set_error("pat_unet_set_gemm_path: null network or path not 0/1"); return PAT_EINVAL; }
+    u->gemm_path = path;
+    return PAT_OK;
+}
+
+extern "C" int pat_unet_status(pat_unet u, int* h_flag, void* stream) {
+    if (!u || !h_flag) { set_error("pat_unet_status: null argument"); return PAT_EINVAL; }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int f = 0;
+    PAT_CUDA(cudaMemcpyAsync(&f, u->status, sizeof(int), cudaMemcpyDeviceToHost, st));
+    PAT_CUDA(cudaStreamSynchronize(st));
+    *h_flag = f & PAT_STATUS_TC05;
+    return PAT_OK;
+}
+
+extern "C" int pat_gemm_bf16(const void* d_A, int lda, const void* d_B, int ldb, int M, int N, int K, float* d_C,
+                             int ldc, int path, int* d_status, void* stream) {
+    if (!d_A || !d_B || !d_C || M < 1 || N < 1 || K < 1 || ldc < N || lda < K || ldb < K || path < 0 || path > 1) {
+        set_error("pat_gemm_bf16: null buffer, size < 1, pitch below the row length or path not 0/1");
+        return PAT_EINVAL;
+    }
+    const auto* A = static_cast<const __nv_bfloat16*>(d_A);
+    const auto* B = static_cast<const __nv_bfloat16*>(d_B);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (path == 1) {
+        if (!unet_gemm_tc05_supported(A, lda, B, ldb, M, N, K)) {
+            set_error("pat_gemm_bf16: the tcgen05 path needs K >= 64, pitches that are multiples of 8 and 16-byte "
+                      "aligned operands");
+            return PAT_EINVAL;
+        }
+        return unet_gemm_tc05(st, A, lda, B, ldb, M, N, K, nullptr, 0, d_C, ldc, 1, 1, d_status);
+    }
+    return unet_gemm(st, A, lda, B, ldb, M, N, K, nullptr, 0, d_C, ldc, 1, 1);
 }

@@ -11,6 +11,11 @@ namespace pat {
 // C[M][N] = A[M][K] . B[N][K]^T (+bias)(ReLU); out_mode 0 bf16, 1 fp32, 2 fp32 atomic add (split K)
 int unet_gemm(cudaStream_t st, const __nv_bfloat16* A, int lda, const __nv_bfloat16* B, int ldb, int M, int N,
               int K, const float* bias, int relu, void* C, int ldc, int out_mode, int splitk);
+// the same GEMM on tcgen05 / TMEM / TMA (unet_tc05.cu); supported: K >= 64, pitches multiples of 8,
+// 16-byte aligned operands.  d_status (may be null) gets PAT_STATUS_TC05 if a bounded wait gave up.
+bool unet_gemm_tc05_supported(const __nv_bfloat16* A, int lda, const __nv_bfloat16* B, int ldb, int M, int N, int K);
+int unet_gemm_tc05(cudaStream_t st, const __nv_bfloat16* A, int lda, const __nv_bfloat16* B, int ldb, int M, int N,
+                   int K, const float* bias, int relu, void* C, int ldc, int out_mode, int splitk, int* d_status);
 int unet_im2col(cudaStream_t st, const __nv_bfloat16* in, __nv_bfloat16* col, int B, int H, int W, int C, int ldc_in,
                 int flip);
 int unet_transpose(cudaStream_t st, const __nv_bfloat16* in, __nv_bfloat16* out, int R, int C, int ld);

@@ -40,6 +40,22 @@ class UNet:
                 pass
             self._h = None
 
+    @property
+    def gemm_path(self) -> int:
+        return getattr(self, "_gemm_path", 0)
+
+    @gemm_path.setter
+    def gemm_path(self, path: int):
+        """0: warp-level tensor cores (mma.sync); 1: tcgen05 / TMEM / TMA (pat_unet_set_gemm_path)."""
+        B.check(B.lib().pat_unet_set_gemm_path(self._h, int(path)), "pat_unet_set_gemm_path")
+        self._gemm_path = int(path)
+
+    def status(self, stream=None) -> int:
+        """PAT_STATUS_TC05 if a bounded wait of a tcgen05 GEMM gave up (synchronises)."""
+        flag = ctypes.c_int(0)
+        B.check(B.lib().pat_unet_status(self._h, ctypes.byref(flag), _stream(stream)), "pat_unet_status")
+        return int(flag.value)
+
     def set_params(self, params, stream=None):
         p = torch.as_tensor(np.asarray(params, dtype=np.float32), device=self.device).contiguous()
         if p.numel() != self.nparam:
