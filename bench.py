@@ -101,6 +101,8 @@ def parse():
     ap.add_argument("--batch-instances", type=int, default=64)
     ap.add_argument("--batch-iters", type=int, default=2)
     ap.add_argument("--batch-plain", type=int, default=64, help="instances also solved one by one")
+    ap.add_argument("--persistent", action="store_true",
+                    help="--batch: forward sweeps of the batched arm as persistent launches")
     ap.add_argument("--roofline-k", type=int, default=0,
                     help="per-pass bandwidth of forward steps with this many data sets on the headline grid "
                          "(working set beyond L2 for K >= 64); uses --nt and --variant")
@@ -110,6 +112,8 @@ def parse():
                     help="simple-phantom experiment of Sec. 4.1: data on a fine grid (no inverse crime), joint "
                          "reconstruction with K=4 data sets against K=1 over four multigrid levels")
     ap.add_argument("--t2-iters", type=int, default=30, help="L-BFGS iterations per level in --table2")
+    ap.add_argument("--gemm", action="store_true",
+                    help="BF16 GEMM of the warm-start network: tcgen05 against the warp-level path (TFLOP/s)")
     ap.add_argument("--warmstart", action="store_true",
                     help="learned warm start: train the U-Net on solver-generated pairs, compare with the plain start")
     ap.add_argument("--ws-train", type=int, default=20000)
@@ -742,7 +746,8 @@ def run_batch(args):
                            c_init=f32(np.full((n, n), 0.5 * (c.min() + c.max()))))
             k0 += K
         data[("cfg", n)] = ReconConfig(levels=(n // 2, n), L=n * dx, dt_data=gs.dt, nt_data=nt, sensors_xy=xy, K=1,
-                                       iters=args.batch_iters, mem=20, ckpt_every=32, autotune=True)
+                                       iters=args.batch_iters, mem=20, ckpt_every=32, autotune=True,
+                                       persistent=args.persistent)
     torch.cuda.synchronize()
     # batched: one call per grid side, the sides concurrently on their own streams
     lat = {}
@@ -780,17 +785,19 @@ def run_batch(args):
                 nt_l = int(round((7 * n - 1) * (lvl_n / n))) + 1
                 cell_steps += ng * ng * K * (nt_l - 1) * (r["trials"] + 3)
     # plain GPU: the same instances one at a time, no batching, no graphs, default variant
-    plain = {}
+    plain, plain_arrival = {}, {}
     tp0 = time.perf_counter()
     for n, members in groups.items():
         for i, K in members[: max(1, args.batch_plain * len(members) // len(specs))]:
             cfg = data[("cfg", n)]
             cfg.K = K
             cfg.autotune = False
+            cfg.persistent = False
             t1 = time.perf_counter()
             reconstruct(cfg, data[i]["y_meas"], data[i]["w"], data[i]["c_init"])
             torch.cuda.synchronize()
             plain[i] = (time.perf_counter() - t1) * 1e3
+            plain_arrival[i] = (time.perf_counter() - tp0) * 1e3
     plain_wall = time.perf_counter() - tp0
     lats = sorted(lat.values())
     pl = sorted(plain.values())
@@ -804,6 +811,13 @@ def run_batch(args):
             "wall_s": wall, "latency_ms_p50": q(lats, 50), "latency_ms_p99": q(lats, 99),
             "plain_wall_s_scaled": plain_wall / frac if frac > 0 else None,
             "plain_latency_ms_p50": q(pl, 50), "plain_latency_ms_p99": q(pl, 99),
+            "latency_note": "all instances arrive together: the batched latency is the time until the batched "
+                            "call of the instance's grid side returns; plain_latency_* is each reconstruction's "
+                            "own duration and plain_arrival_latency_* the time from the common arrival until it "
+                            "is done when they are served one after another",
+            "plain_arrival_latency_ms_p50": q(sorted(plain_arrival.values()), 50),
+            "plain_arrival_latency_ms_p99": q(sorted(plain_arrival.values()), 99),
+            "persistent_sweeps": bool(args.persistent),
             "plain_instances_timed": len(plain), "gpu_launches": batched_launches,
             "speedup_vs_plain": (plain_wall / frac) / wall if frac > 0 else None}
     print(json.dumps(line), flush=True)
@@ -1056,6 +1070,66 @@ def run_warmstart(args):
     print(json.dumps(line), flush=True)
 
 
+def run_gemm(args):
+    """TFLOP/s of the network's BF16 GEMM on both tensor-core paths (pat_gemm_bf16), on a large
+    square product and on the shapes of the U-Net's convolutions at 128 x 128, batch 32."""
+    import ctypes
+
+    import torch
+
+    import paper_2505_08482_gb300 as pkg
+    from paper_2505_08482_gb300 import _binding as B
+    pkg.build()
+    torch.cuda.set_device(0)
+    L = B.lib()
+    peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    bf16_peak = float(peak.get("bf16_tflops", 1900.0))
+    P = 32 * 128 * 128
+    shapes = [("square 8192", 8192, 8192, 8192), ("square 4096", 4096, 4096, 4096),
+              ("conv 3x3 32->32 fwd", P, 32, 288), ("conv 3x3 64->64 fwd (64^2)", P // 4, 64, 576),
+              ("conv 3x3 256->256 fwd (16^2)", P // 64, 256, 2304), ("weight grad 32x288 over pixels", 32, 288, P)]
+    rows = []
+    st = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+    for name, M, N, K in shapes:
+        A = torch.randn((M, K), device="cuda").to(torch.bfloat16)
+        Bm = torch.randn((N, K), device="cuda").to(torch.bfloat16)
+        C = torch.empty((M, N), dtype=torch.float32, device="cuda")
+        status = torch.zeros((1,), dtype=torch.int32, device="cuda")
+        row = {"shape": name, "M": M, "N": N, "K": K}
+        for path in (0, 1):
+            def call():
+                rc = L.pat_gemm_bf16(ctypes.c_void_p(A.data_ptr()), K, ctypes.c_void_p(Bm.data_ptr()), K, M, N, K,
+                                     ctypes.c_void_p(C.data_ptr()), N, path, ctypes.c_void_p(status.data_ptr()),
+                                     ctypes.c_void_p(st.cuda_stream))
+                assert rc == 0, L.pat_last_error()
+            for _ in range(3):
+                call()
+            torch.cuda.synchronize()
+            reps = 10
+            ts = []
+            for _ in range(reps):
+                flush.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(st)
+                call()
+                e1.record(st)
+                torch.cuda.synchronize()
+                ts.append(e0.elapsed_time(e1))
+            ms = statistics.median(ts)
+            tf = 2.0 * M * N * K / (ms * 1e-3) / 1e12
+            row[f"path{path}"] = {"ms": ms, "tflops": tf, "frac_of_bf16_peak": tf / bf16_peak}
+        row["status"] = int(status.item())
+        row["tcgen05_speedup"] = row["path0"]["ms"] / row["path1"]["ms"]
+        rows.append(row)
+        del A, Bm, C
+    print(json.dumps({"metric": "BF16 GEMM TFLOP/s (C = A B^T, FP32 accumulation)", "unit": "TFLOP/s",
+                      "bf16_peak_tflops": bf16_peak, "peak_kind": "measured bf16_tflops (burst)",
+                      "paths": {"0": "mma.sync m16n8k16 (warp level)", "1": "tcgen05.mma + TMEM + TMA"},
+                      "l2": "256 MiB written between timed calls", "rows": rows}), flush=True)
+
+
 def ctypes_read(L):
     import ctypes
     tot = ctypes.c_double(0.0)
@@ -1079,6 +1153,9 @@ def main():
         return
     if args.warmstart:
         run_warmstart(args)
+        return
+    if args.gemm:
+        run_gemm(args)
         return
     if args.roofline_k:
         run_roofline_k(args)

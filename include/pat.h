@@ -354,6 +354,8 @@ typedef struct {
     double prior_tau;
     double prior_eta_c, prior_sigma_c;
     double prior_eta_p0, prior_sigma_p0;
+    int persistent;  /* nonzero: forward sweeps of every level whose grid side has one run as one
+                        persistent launch (pat_plan_set_persistent); other sides keep the passes */
 } pat_recon_cfg;
 
 /* One row per L-BFGS iteration. */

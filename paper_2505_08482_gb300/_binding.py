@@ -50,7 +50,7 @@ class PatReconCfg(ctypes.Structure):
                 ("mem", c_int), ("iters", c_int), ("max_halvings", c_int), ("ckpt_every", c_int),
                 ("rtol", c_double), ("alpha0", c_double), ("c1", c_double), ("sigma_p0", c_double),
                 ("autotune", c_int), ("prior_tau", c_double), ("prior_eta_c", c_double), ("prior_sigma_c", c_double),
-                ("prior_eta_p0", c_double), ("prior_sigma_p0", c_double)]
+                ("prior_eta_p0", c_double), ("prior_sigma_p0", c_double), ("persistent", c_int)]
 
 
 class PatInstance(ctypes.Structure):

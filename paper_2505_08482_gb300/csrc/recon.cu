@@ -240,6 +240,7 @@ int Batch::level(int li, const float* const* xprev, int nprev) {
     // forward-step timing (a short run on the forward part of the workspace): the gradient
     // timing of six whole evaluations per level would cost more than it saves here
     if (cfg.autotune) RC(pat_plan_autotune(plan, ws, pat_workspace_bytes(plan, PAT_WS_FORWARD), nullptr, st));
+    if (cfg.persistent && pat_plan_set_persistent(plan, 1) != PAT_OK) pat_plan_set_persistent(plan, 0);
     if (prior) pat_prior_destroy(prior);
     prior = nullptr;
     if (cfg.prior_tau > 0) {

@@ -356,6 +356,7 @@ class ReconConfig:
     prior_sigma_c: float = 0.0
     prior_eta_p0: float = 0.0
     prior_sigma_p0: float = 0.0
+    persistent: bool = False   # forward sweeps as one persistent launch where the grid side has one
 
 
 def _cfg_struct(cfg: ReconConfig, K: int, xy):
@@ -365,7 +366,7 @@ def _cfg_struct(cfg: ReconConfig, K: int, xy):
                           cfg.p0_lo, cfg.c_bg, cfg.rho0, cfg.pml_alpha, cfg.min_pml, cfg.mem, cfg.iters,
                           cfg.max_halvings, cfg.ckpt_every, cfg.rtol, cfg.alpha0, cfg.c1, cfg.sigma_p0,
                           int(bool(cfg.autotune)), cfg.prior_tau, cfg.prior_eta_c, cfg.prior_sigma_c,
-                          cfg.prior_eta_p0, cfg.prior_sigma_p0)
+                          cfg.prior_eta_p0, cfg.prior_sigma_p0, int(bool(cfg.persistent)))
     return c_cfg, lv
 
 

@@ -26,7 +26,7 @@ def _cfg(B, **kw):
                       cfl=0.3, c_lo=1350.0, c_hi=1750.0, p0_lo=0.0, c_bg=1500.0, rho0=1000.0, pml_alpha=2.0,
                       min_pml=20, mem=20, iters=5, max_halvings=20, ckpt_every=32, rtol=1e-4, alpha0=0.1, c1=1e-4,
                       sigma_p0=0.25, autotune=0, prior_tau=0.0, prior_eta_c=0.0, prior_sigma_c=0.0,
-                      prior_eta_p0=0.0, prior_sigma_p0=0.0)
+                      prior_eta_p0=0.0, prior_sigma_p0=0.0, persistent=0)
     c._keep = (levels, xy)
     for k, v in kw.items():
         setattr(c, k, v)
