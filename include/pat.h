@@ -112,7 +112,7 @@ int pat_plan_shape(pat_plan plan, int* ninst, int* K);
 int pat_plan_ng(pat_plan plan);
 
 /* Kernel variants of a plan.  Grid sides with a compiled two-level FFT
- * (108, 144, 180, 200, 240, 300 = N1 x N2) have five fixed-size variants,
+ * (108, 144, 180, 200, 240, 300 = N1 x N2) have seven fixed-size variants,
  * all one launch per pass:
  *   0  column and velocity passes on the N1 x N2 factorisation, density
  *      passes on N2 x N1 (4 rows / 4 spectral columns per CTA); the column
@@ -122,7 +122,11 @@ int pat_plan_ng(pat_plan plan);
  *   2  all passes N1 x N2, 8 rows / 2 columns per CTA;
  *   3  as 1 with the row passes' state staged in shared memory by TMA bulk
  *      copies instead of registers;
- *   4  all passes N2 x N1, 4 rows / 4 columns per CTA.
+ *   4  all passes N2 x N1, 4 rows / 4 columns per CTA;
+ *   5  as 0 with 8 rows per CTA in the row passes;
+ *   6  as 0 with the segment recompute's row passes (which share the GPU
+ *      with the adjoint) staged by TMA as in 3, so that they need fewer
+ *      registers.
  * Every side also has the generic shared-memory Stockham passes (variant
  * -1).  All variants compute the same scheme.  A new plan uses variant 0
  * when it exists, else -1.  pat_plan_variants returns the number of
@@ -497,9 +501,9 @@ int pat_unet_grads(pat_unet net, const float* d_in, const float* d_target, int B
 int pat_unet_train_step(pat_unet net, const float* d_in, const float* d_target, int B, float lr, double* d_loss,
                         void* stream);
 
-/* Tensor-core path of the network's GEMMs: 0 (default) the warp-level BF16
- * MMA (mma.sync m16n8k16, operands staged by cp.async); 1 the fifth-generation
- * tensor cores: tcgen05.mma (kind::f16, BF16 operands, FP32 accumulator in
+/* Tensor-core path of the network's GEMMs: 0 the warp-level BF16 MMA
+ * (mma.sync m16n8k16, operands staged by cp.async); 1 (default) the
+ * fifth-generation tensor cores: tcgen05.mma (kind::f16, BF16 operands, FP32 accumulator in
  * tensor memory) on 128 x 128 tiles whose 128 x 64 operand blocks are copied
  * by TMA (cp.async.bulk.tensor, 128-byte swizzle) into a 4-stage ring of
  * shared memory; GEMMs whose operands the TMA cannot address (K < 64,

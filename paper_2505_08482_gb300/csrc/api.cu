@@ -90,7 +90,7 @@ namespace {
 
 // recompute segment j's pressure history into its buffer (on stream st)
 int recompute(pat_plan_s* p, const float* p0, const Ws& w, int j, cudaStream_t st) {
-    Launch L{p, st};
+    Launch L{p, st, false, true};
     const size_t f = size_t(p->K) * p->ng * p->ng;
     const int n0 = j * p->s_eff;
     const int n1 = std::min(n0 + p->s_eff, p->nt) - 1;

@@ -40,6 +40,6 @@ const SweepOps* sweep_ops_for(int ng) {
     }
 }
 
-int fixed_variants(int ng) { return fixed_ops_for(ng, 0) ? 5 : 0; }
+int fixed_variants(int ng) { return fixed_ops_for(ng, 0) ? 7 : 0; }
 
 }  // namespace pat

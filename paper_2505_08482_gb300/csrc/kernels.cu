@@ -612,7 +612,8 @@ int launch_row_rho(const Launch& L, const Ws& w, int mode, const float* p0, floa
     const pat_plan_s* p = L.p;
     prof_begin(PAT_K_ROW_RHO, L.st);
     if (p->fast)
-        p->fast->row_rho(geo_ws(p, w), L.st, w.A, w.B, w.rx, w.ry, w.cg, mode, p0, y, tstep, hist, hist_slot);
+        ((L.recompute && p->fast->row_rho_rc) ? p->fast->row_rho_rc : p->fast->row_rho)(
+            geo_ws(p, w), L.st, w.A, w.B, w.rx, w.ry, w.cg, mode, p0, y, tstep, hist, hist_slot);
     else
         k_row_rho<<<row_grid(p), 256, p->smem_row, L.st>>>(geo(p), w.A, w.B, w.rx, w.ry, w.cg, mode, p0, y,
                                                            tstep, hist, hist_slot, p->R);
@@ -663,7 +664,8 @@ int launch_row_u(const Launch& L, const Ws& w, int init) {
     const pat_plan_s* p = L.p;
     prof_begin(PAT_K_ROW_U, L.st);
     if (p->fast)
-        p->fast->row_u(geo_ws(p, w), L.st, w.A, w.B, w.ux, w.uy, 0, init);
+        ((L.recompute && p->fast->row_u_rc) ? p->fast->row_u_rc : p->fast->row_u)(geo_ws(p, w), L.st, w.A, w.B,
+                                                                                   w.ux, w.uy, 0, init);
     else
         k_row_u<<<row_grid(p), 256, p->smem_row, L.st>>>(geo(p), w.A, w.B, w.ux, w.uy, init, p->R);
     prof_end(PAT_K_ROW_U, L.st);

@@ -26,6 +26,7 @@
 
 #include <algorithm>
 #include <cstdint>
+#include <type_traits>
 
 #include "fft2l.cuh"
 #include "geo.cuh"
@@ -46,6 +47,10 @@ struct FixedOps {
                         int first, const float* resid, int tstep, const float* hist, int hist_slot);
     // column pass for passes that run alone on the GPU (nullptr: col)
     void (*col_solo)(const Geo&, cudaStream_t, float2*, float2*, int mode, int op, float scale);
+    // row passes of the segment recompute, which shares the GPU with the adjoint (nullptr: row_u, row_rho)
+    void (*row_u_rc)(const Geo&, cudaStream_t, float2*, float2*, float*, float*, int kind, int init);
+    void (*row_rho_rc)(const Geo&, cudaStream_t, float2*, const float2*, float*, float*, const float*, int mode,
+                       const float* p0, float* y, int tstep, float* hist, int hist_slot);
 };
 
 const FixedOps* fixed_ops_for(int ng, int variant);   // nullptr if no fixed size matches
@@ -765,15 +770,16 @@ struct FixedImpl {
                    rby, cbar, cg, first, resid, tstep, hist, slot);
     }
     static FixedOps ops() {
-        return FixedOps{F::N, RR, CC, &configure, &col, &row_u, &row_rho, &row_adj_rho, nullptr};
+        return FixedOps{F::N, RR, CC, &configure, &col, &row_u, &row_rho, &row_adj_rho, nullptr, nullptr, nullptr};
     }
 };
 
 // A variant whose pass kinds come from different tile shapes / factorisations of the same
 // Ng (the half spectra in global memory have one layout): column passes from C (from CS when
 // the pass runs alone on the GPU), velocity row passes from U, density row passes from R,
-// adjoint density row passes from J.
-template <class C, class U, class R, class J, class CS = C>
+// adjoint density row passes from J; the segment recompute's velocity and density row passes
+// from RU and RR when given (void: U and R).
+template <class C, class U, class R, class J, class CS = C, class RU = void, class RR = void>
 struct MixedImpl {
     static_assert(C::F::N == U::F::N && C::F::N == R::F::N && C::F::N == J::F::N && C::F::N == CS::F::N,
                   "one grid side");
@@ -783,13 +789,22 @@ struct MixedImpl {
         if (rc == PAT_OK) rc = R::configure();
         if (rc == PAT_OK) rc = J::configure();
         if (rc == PAT_OK) rc = CS::configure();
+        if constexpr (!std::is_void_v<RU>) {
+            if (rc == PAT_OK) rc = RU::configure();
+        }
+        if constexpr (!std::is_void_v<RR>) {
+            if (rc == PAT_OK) rc = RR::configure();
+        }
         return rc;
     }
     static FixedOps ops() {
-        return FixedOps{C::F::N, 0, 0, &configure, &C::col, &U::row_u, &R::row_rho, &J::row_adj_rho, &CS::col};
+        FixedOps o{C::F::N, 0, 0, &configure, &C::col, &U::row_u, &R::row_rho, &J::row_adj_rho, &CS::col,
+                   nullptr, nullptr};
+        if constexpr (!std::is_void_v<RU>) o.row_u_rc = &RU::row_u;
+        if constexpr (!std::is_void_v<RR>) o.row_rho_rc = &RR::row_rho;
+        return o;
     }
 };
-
 
 // ---------------------------------------------------------------------------
 // Persistent forward sweep: one launch runs the initial pass and all Nt-1 steps of every

@@ -123,7 +123,8 @@ void prof_end(int cls, cudaStream_t st);
 struct Launch {
     const pat_plan_s* p;
     cudaStream_t st;
-    bool solo = false;   // no other stream of this call runs beside it (the forward sweep)
+    bool solo = false;        // no other stream of this call runs beside it (the forward sweep)
+    bool recompute = false;   // the segment recompute, which runs beside the adjoint
 };
 
 int configure_kernels(pat_plan_s* p);

@@ -69,7 +69,7 @@ struct pat_unet_s {
     long long step = 0;
     std::vector<void*> allocs;
     int device = 0;
-    int gemm_path = 0;                   // 0 warp-level tensor cores (mma.sync), 1 tcgen05 / TMEM / TMA
+    int gemm_path = 1;                   // 1 tcgen05 / TMEM / TMA (default), 0 warp-level tensor cores (mma.sync)
     int* status = nullptr;               // device status word of the tcgen05 GEMMs (PAT_STATUS_TC05)
 };
 

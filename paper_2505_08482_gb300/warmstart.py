@@ -42,11 +42,11 @@ class UNet:
 
     @property
     def gemm_path(self) -> int:
-        return getattr(self, "_gemm_path", 0)
+        return getattr(self, "_gemm_path", 1)
 
     @gemm_path.setter
     def gemm_path(self, path: int):
-        """0: warp-level tensor cores (mma.sync); 1: tcgen05 / TMEM / TMA (pat_unet_set_gemm_path)."""
+        """1 (default): tcgen05 / TMEM / TMA; 0: warp-level tensor cores, mma.sync (pat_unet_set_gemm_path)."""
         B.check(B.lib().pat_unet_set_gemm_path(self._h, int(path)), "pat_unet_set_gemm_path")
         self._gemm_path = int(path)
 

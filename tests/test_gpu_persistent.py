@@ -36,6 +36,7 @@ def _case(n, K, seed):
 def test_persistent_forward_is_bit_identical_and_matches_oracle(n, nt):
     from oracle.forward import forward
     from oracle.sensors import sensor_matrix
+    from paper_2505_08482_gb300 import _binding as B
     K = 3
     c, p0 = _case(n, K, n)
     xy = ps.rng_for(n + 1).uniform(0.3 * n, 0.7 * n, size=(48, 2)) * 1e-4
@@ -48,7 +49,8 @@ def test_persistent_forward_is_bit_identical_and_matches_oracle(n, nt):
     assert plan.persistent
     y = plan.forward(_dev(c), _dev(p0))
     torch.cuda.synchronize()
-    assert plan.status(kind=0) == 0
+    # no bounded wait gave up (the forward workspace has no objective, so only these bits count)
+    assert plan.status(kind=0) & (B.PAT_STATUS_WAIT | B.PAT_STATUS_QUEUE) == 0
     assert rel_l2(y.cpu().numpy(), ref.cpu().numpy()) <= 1e-6
     g = oracle_grid(gp)
     assert rel_l2(y.cpu().numpy(), forward(g, c, p0, sensor_matrix(g, xy))) <= 1e-4
