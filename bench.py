@@ -112,6 +112,9 @@ def parse():
                     help="simple-phantom experiment of Sec. 4.1: data on a fine grid (no inverse crime), joint "
                          "reconstruction with K=4 data sets against K=1 over four multigrid levels")
     ap.add_argument("--t2-iters", type=int, default=30, help="L-BFGS iterations per level in --table2")
+    ap.add_argument("--profile-eval", type=int, default=0,
+                    help="profiling runs: this many gradient evaluations of the workload (variant from --variant, "
+                         "default 0; no autotuning, no timing) after one warm-up evaluation, then exit")
     ap.add_argument("--gemm", action="store_true",
                     help="BF16 GEMM of the warm-start network: tcgen05 against the warp-level path (TFLOP/s)")
     ap.add_argument("--warmstart", action="store_true",
@@ -1130,6 +1133,39 @@ def run_gemm(args):
                       "l2": "256 MiB written between timed calls", "rows": rows}), flush=True)
 
 
+def run_profile_eval(args):
+    """Gradient evaluations of the headline workload for ncu captures: one warm-up evaluation
+    (its launches are counted and printed so that a capture can skip them), then
+    --profile-eval evaluations; eager launches, no autotuning, no timing."""
+    import numpy as np
+    import torch
+
+    import paper_2505_08482_gb300 as pkg
+    from paper_2505_08482_gb300 import _binding as B
+    from paper_2505_08482_gb300.solver import GridSpec, Plan
+    pkg.build()
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    L = B.lib()
+    w, c_init = inputs(0)
+    n, K, M, nt = WL["n"], WL["K"], WL["M"], args.nt
+    gs = GridSpec(n=n, pml=pml_auto(n), dx=WL["dx"], dt=WL["cfl"] * WL["dx"] / WL["c_hi"], nt=nt, c_ref=WL["c_hi"])
+    plan = Plan(gs, w.sensors, K, ckpt_every=args.ckpt, device=dev)
+    plan.variant = 0 if args.variant is None else args.variant
+    f32 = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float32, device=dev)
+    c0, p0 = f32(np.full((n, n), c_init)), f32(0.5 * w.p0_true)
+    ym = f32(np.random.default_rng(0).standard_normal((K, nt, M)) * 0.01)
+    wt = f32(np.ones(K))
+    l0 = L.pat_kernel_launches()
+    plan.adjoint_grad(c0, p0, ym, wt)
+    torch.cuda.synchronize()
+    print(f"launches_per_eval={L.pat_kernel_launches() - l0} (the library's kernels; memsets and copies are not "
+          f"kernels)", file=sys.stderr, flush=True)
+    for _ in range(args.profile_eval):
+        plan.adjoint_grad(c0, p0, ym, wt)
+    torch.cuda.synchronize()
+
+
 def ctypes_read(L):
     import ctypes
     tot = ctypes.c_double(0.0)
@@ -1156,6 +1192,9 @@ def main():
         return
     if args.gemm:
         run_gemm(args)
+        return
+    if args.profile_eval:
+        run_profile_eval(args)
         return
     if args.roofline_k:
         run_roofline_k(args)

@@ -69,6 +69,8 @@ __device__ __forceinline__ float2 ld_spec(const float2* p) { return __ldcg(p); }
 // a launched pass has no checkpoint target.
 struct LaunchedCtx {
     int bx, k;
+    // state rows written by earlier kernels of the stream: ordinary loads
+    __device__ __forceinline__ float ld(const float* p) const { return *p; }
     __device__ __forceinline__ void state_ready() const {}
     __device__ __forceinline__ void input_ready() const { pdl_wait_then_release(); }
     __device__ __forceinline__ float* ck_a() const { return nullptr; }
@@ -302,8 +304,8 @@ __device__ __forceinline__ void row_u_body(const Geo& g, const Ctx& ctx, float2*
         static_for<0, N1>([&](auto I) {
             constexpr int n1 = decltype(I)::value;
             const int x = idx + N2 * n1;
-            sx[n1] = zero ? 0.f : __ldcg(uxr + x);
-            sy[n1] = zero ? 0.f : __ldcg(uyr + x);
+            sx[n1] = zero ? 0.f : ctx.ld(uxr + x);
+            sy[n1] = zero ? 0.f : ctx.ld(uyr + x);
             fa[n1] = g.a_stag[x];
         });
     }
@@ -331,8 +333,8 @@ __device__ __forceinline__ void row_u_body(const Geo& g, const Ctx& ctx, float2*
                 uy0 = zero ? 0.f : Sy[r * N + x];
             } else if constexpr (LATE) {   // fetched where used (fewer registers)
                 ax = g.a_stag[x];
-                ux0 = zero ? 0.f : __ldcg(uxr + x);
-                uy0 = zero ? 0.f : __ldcg(uyr + x);
+                ux0 = zero ? 0.f : ctx.ld(uxr + x);
+                uy0 = zero ? 0.f : ctx.ld(uyr + x);
             } else {
                 ax = fa[n1];
                 ux0 = sx[n1];
@@ -432,8 +434,8 @@ __device__ __forceinline__ void row_rho_body(const Geo& g, const Ctx& ctx, float
             const int x = idx + N2 * n1;
             cc[n1] = cr[x];
             fa[n1] = g.a_cell[x];
-            s0[n1] = mode == 1 ? p0_at(x) : __ldcg(rxr + x);
-            s1[n1] = mode == 1 ? 0.f : __ldcg(ryr + x);
+            s0[n1] = mode == 1 ? p0_at(x) : ctx.ld(rxr + x);
+            s1[n1] = mode == 1 ? 0.f : ctx.ld(ryr + x);
         });
     }
     const float acy = g.a_cell[yy];
@@ -465,8 +467,8 @@ __device__ __forceinline__ void row_rho_body(const Geo& g, const Ctx& ctx, float
             } else if constexpr (LATE) {   // fetched where used (fewer registers)
                 c = cr[x];
                 acx = g.a_cell[x];
-                v0 = mode == 1 ? p0_at(x) : __ldcg(rxr + x);
-                v1 = mode == 1 ? 0.f : __ldcg(ryr + x);
+                v0 = mode == 1 ? p0_at(x) : ctx.ld(rxr + x);
+                v1 = mode == 1 ? 0.f : ctx.ld(ryr + x);
             } else {
                 c = cc[n1];
                 acx = fa[n1];
@@ -847,6 +849,8 @@ struct QueueCtx {
     float* cka;                   // checkpoint targets of the velocity / density rows, or null
     float* ckb;
     unsigned long long wait_ns;
+    // state rows written by other CTAs of the same launch: L2 loads (the SM's L1 may hold old lines)
+    __device__ __forceinline__ float ld(const float* p) const { return __ldcg(p); }
     __device__ __forceinline__ void wait(int need) const {
         if (threadIdx.x == 0) {
             const volatile int* done = queue + 2 + k;
