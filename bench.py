@@ -1134,9 +1134,9 @@ def run_gemm(args):
 
 
 def run_profile_eval(args):
-    """Gradient evaluations of the headline workload for ncu captures: one warm-up evaluation
-    (its launches are counted and printed so that a capture can skip them), then
-    --profile-eval evaluations; eager launches, no autotuning, no timing."""
+    """Gradient evaluations of the headline workload for ncu captures: one warm-up evaluation,
+    then --profile-eval evaluations inside the NVTX range "profiled"; eager launches, no
+    autotuning, no timing."""
     import numpy as np
     import torch
 
@@ -1161,9 +1161,11 @@ def run_profile_eval(args):
     torch.cuda.synchronize()
     print(f"launches_per_eval={L.pat_kernel_launches() - l0} (the library's kernels; memsets and copies are not "
           f"kernels)", file=sys.stderr, flush=True)
+    torch.cuda.nvtx.range_push("profiled")   # ncu --nvtx --nvtx-include "profiled/" captures these
     for _ in range(args.profile_eval):
         plan.adjoint_grad(c0, p0, ym, wt)
     torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
 
 
 def ctypes_read(L):
