@@ -232,12 +232,14 @@ def init_params(levels, base, in_ch, seed=0) -> np.ndarray:
     return np.concatenate(out).astype(np.float32)
 
 
-def iterations_to(rows, target, nlevels):
-    """(iterations over all levels, ms) until E_c <= target on the finest level, or (None, None)."""
+def iterations_to(rows, target, nlevels, ep0_target=None):
+    """(iterations over all levels, ms) until E_c <= target (and E_p0 <= ep0_target if given) on the
+    finest level, or (None, None)."""
     its, ms = 0, 0.0
     for r in rows:
         its += 1
         ms += r["ms"]
-        if r["level"] == nlevels - 1 and 0 <= r["Ec"] <= target:
+        if r["level"] == nlevels - 1 and 0 <= r["Ec"] <= target and (
+                ep0_target is None or 0 <= r.get("Ep0", -1.0) <= ep0_target):
             return its, ms
     return None, None
