@@ -161,7 +161,8 @@ int pat_plan_persistent(pat_plan plan);
 int pat_plan_set_graphs(pat_plan plan, int enable);
 
 /* Autotuner: times every variant of the plan (generic and fixed-size) on
- * this GPU and keeps the fastest.  With a gradient workspace (ws_bytes >=
+ * this GPU and keeps the fastest (median of three timings per variant).
+ * With a gradient workspace (ws_bytes >=
  * PAT_WS_GRADIENT size) it times one whole gradient evaluation per variant
  * (forward sweep with checkpoints, reverse sweep with the recompute stream;
  * c = c_ref, p0 = 0, zero residual), otherwise 32 forward steps on a forward

@@ -23,9 +23,13 @@ Contents (paper sections in brackets):
 * ``multigrid`` coarse-to-fine schedule, prolongation, data time interpolation
                 (Sec. 3.1, Sec. 4.1.2)
 * ``metrics``   relative errors (Eq. RelativeError)
+* ``prior``     Ornstein-Uhlenbeck prior terms with a dense Cholesky factor (Eq.
+                Minimised_functional, Sec. 4.1.2)
+* ``unet``      plain-PyTorch CPU reference of the warm-start network (no paper
+                counterpart; imported on its own, it needs torch)
 
 Every function is pinned by a ``-m "not gpu"`` test against closed forms,
 invariants, finite differences or library routines; none is "parity
 unpinned".
 """
-from . import grid, sensors, forward, adjoint, lbfgs, multigrid, metrics  # noqa: F401
+from . import grid, sensors, forward, adjoint, lbfgs, multigrid, metrics, prior  # noqa: F401

@@ -331,20 +331,25 @@ extern "C" int pat_plan_autotune(pat_plan p, void* ws, size_t ws_bytes, double* 
         if (rc != PAT_OK) break;
         rc = run_steps(L, w, 1, 4, nullptr, nullptr, 0);   // first launches of the variant's kernels
         if (rc != PAT_OK) break;
-        cudaEventRecord(e0, st);
-        if (grad) {
-            rc = forward_sweep(p, c, p0, w.ypred, w, true, st);
-            if (rc == PAT_OK) rc = reverse_sweep(p, p0, w.resid, gp0, gc, w, true, st);
-        } else {
-            rc = run_steps(L, w, 1, 1 + nsteps, nullptr, nullptr, 0);
+        // the median of kSamples timings, so that one disturbed sample cannot decide the choice
+        constexpr int kSamples = 3;
+        float samples[kSamples];
+        for (int r = 0; r < kSamples && rc == PAT_OK; ++r) {
+            cudaEventRecord(e0, st);
+            if (grad) {
+                rc = forward_sweep(p, c, p0, w.ypred, w, true, st);
+                if (rc == PAT_OK) rc = reverse_sweep(p, p0, w.resid, gp0, gc, w, true, st);
+            } else {
+                rc = run_steps(L, w, 1, 1 + nsteps, nullptr, nullptr, 0);
+            }
+            cudaEventRecord(e1, st);
+            if (rc != PAT_OK) break;
+            if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&samples[r], e0, e1) != cudaSuccess)
+                rc = cuda_fail(cudaGetLastError(), "pat_plan_autotune timing");
         }
-        cudaEventRecord(e1, st);
         if (rc != PAT_OK) break;
-        float ms = 0.f;
-        if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
-            rc = cuda_fail(cudaGetLastError(), "pat_plan_autotune timing");
-            break;
-        }
+        std::sort(samples, samples + kSamples);
+        const float ms = samples[kSamples / 2];
         const double per = grad ? double(ms) : double(ms) / nsteps;
         if (h_ms) h_ms[v + 1] = per;
         if (per < best) {
