@@ -160,6 +160,41 @@ struct Fft2 {
             Z[(k1 * P2 + n2) * S] = v;
         });
     }
+    // The two twiddled steps with the twiddles in a per-layout table, laid out so that the
+    // threads of one step read consecutive entries (no shared-memory bank conflicts; the
+    // natural-order table is read with stride k1 or n2 across threads):
+    // twA[k1 N2 + n2] = twB[n2 N1 + k1] = W_N^{n2 k1}.  Same values, same results.
+    template <int S = 1>
+    __host__ __device__ static __forceinline__ void fwd_a_t(float2 (&a)[N1], int n2, float2* Z, const float2* twA) {
+        dft<N1, false>(a);
+        static_for<0, N1>([&](auto kI) {
+            constexpr int k1 = decltype(kI)::value;
+            float2 v = a[k1];
+            if constexpr (k1 > 0) v = cmul(v, twA[k1 * N2 + n2]);
+            Z[(k1 * P2 + n2) * S] = v;
+        });
+    }
+    template <int S = 1>
+    __host__ __device__ static __forceinline__ void inv_b_t(float2 (&b)[N2], int k1, float2* Z, const float2* twB) {
+        dft<N2, true>(b);
+        static_for<0, N2>([&](auto nI) {
+            constexpr int n2 = decltype(nI)::value;
+            float2 v = b[n2];
+            if constexpr (n2 > 0) v = cmulc(v, twB[n2 * N1 + k1]);
+            Z[(k1 * P2 + n2) * S] = v;
+        });
+    }
+    // twA and twB (N entries each) from the natural-order table tw; entries i = tid, tid + nthr, ...
+    __host__ __device__ static __forceinline__ void fill_tables(float2* twA, float2* twB, const float2* tw, int tid,
+                                                                int nthr) {
+        for (int i = tid; i < N; i += nthr) {
+            const int ka = i / N2, na = i - ka * N2;
+            twA[i] = tw[na * ka];
+            const int nb = i / N1, kb = i - nb * N1;
+            twB[i] = tw[nb * kb];
+        }
+    }
+
     // inverse, A layout: a[k1] = Z[k1 P2 + n2] -> inverse DFT_N1 -> a[n1] = x[n2 + N2 n1]
     template <int S = 1>
     __host__ __device__ static __forceinline__ void inv_a_load(float2 (&a)[N1], int n2, const float2* Z) {

@@ -241,12 +241,12 @@ __device__ __forceinline__ void finish_fwd(float2* Zs, int idx, bool active) {
     __syncthreads();
 }
 
-// Shared memory of the row passes: twiddles, two transpose buffers and RR real rows
+// Shared memory of the row passes: the two twiddle tables, two transpose buffers and RR real rows
 // (base); staged: then ns arrays of RR rows, the PML factors, nc arrays of RR domain
 // rows of width n, and the mbarrier.
 template <class F, int RR>
 struct RowSmem {
-    static constexpr size_t base = (F::N + 2 * RR * F::ZS) * sizeof(float2) + RR * F::N * sizeof(float);
+    static constexpr size_t base = (2 * F::N + 2 * RR * F::ZS) * sizeof(float2) + RR * F::N * sizeof(float);
     static constexpr size_t staged(int ns, int nc, int n) {
         return base + (size_t(ns) * RR + 1) * F::N * sizeof(float) + size_t(nc) * RR * n * sizeof(float) + 16;
     }
@@ -269,8 +269,9 @@ __device__ __forceinline__ void row_u_body(const Geo& g, const Ctx& ctx, float2*
     using F = Fft2<N1, N2>;
     constexpr int N = F::N, T = F::T;
     extern __shared__ float2 sm[];
-    float2* tw = sm;
-    float2* Z0 = sm + N;
+    float2* twA = sm;       // twiddles of the A-layout step [N], read with consecutive n2 across threads
+    float2* twB = sm + N;   // twiddles of the B-layout step [N], read with consecutive k1 across threads
+    float2* Z0 = sm + 2 * N;
     float2* Z1 = Z0 + RR * F::ZS;
     float* Sx = reinterpret_cast<float*>(Z1 + RR * F::ZS) + RR * N;   // staged u_x, u_y [RR][N] (after base)
     float* Sy = Sx + RR * N;
@@ -310,12 +311,12 @@ __device__ __forceinline__ void row_u_body(const Geo& g, const Ctx& ctx, float2*
         });
     }
     const float ay = g.a_stag[yy];
-    for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = g.tw[i];
+    F::fill_tables(twA, twB, g.tw, threadIdx.x, blockDim.x);
     ctx.input_ready();
     float2 b[N2];
     if (bact) load_c2r_b<F>(b, idx, A + row * g.hp, B + row * g.hp);
     __syncthreads();
-    if (bact) F::inv_b(b, idx, Z0 + r * F::ZS, tw);
+    if (bact) F::inv_b_t(b, idx, Z0 + r * F::ZS, twB);
     __syncthreads();
     if constexpr (STAGE) mbar_wait(mb, 0, g.status);
     if (aact) {
@@ -361,7 +362,7 @@ __device__ __forceinline__ void row_u_body(const Geo& g, const Ctx& ctx, float2*
                 a[n1] = make_float2(tpx, tpy);
             }
         });
-        F::fwd_a(a, idx, Z1 + r * F::ZS, tw);
+        F::fwd_a_t(a, idx, Z1 + r * F::ZS, twA);
     }
     __syncthreads();
     finish_fwd<F>(Z1 + r * F::ZS, idx, bact);
@@ -388,8 +389,9 @@ __device__ __forceinline__ void row_rho_body(const Geo& g, const Ctx& ctx, float
     using F = Fft2<N1, N2>;
     constexpr int N = F::N, T = F::T;
     extern __shared__ float2 sm[];
-    float2* tw = sm;
-    float2* Z0 = sm + N;
+    float2* twA = sm;       // twiddles of the A-layout step [N], read with consecutive n2 across threads
+    float2* twB = sm + N;   // twiddles of the B-layout step [N], read with consecutive k1 across threads
+    float2* Z0 = sm + 2 * N;
     float2* Z1 = Z0 + RR * F::ZS;
     float* P = reinterpret_cast<float*>(Z1 + RR * F::ZS);   // [RR][N]
     float* Sx = P + RR * N;                                 // staged rho_x, rho_y, c [RR][N] each
@@ -439,12 +441,12 @@ __device__ __forceinline__ void row_rho_body(const Geo& g, const Ctx& ctx, float
         });
     }
     const float acy = g.a_cell[yy];
-    for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = g.tw[i];
+    F::fill_tables(twA, twB, g.tw, threadIdx.x, blockDim.x);
     ctx.input_ready();
     float2 b[N2];
     if (bact) load_c2r_b<F>(b, idx, A + row * g.hp, B + row * g.hp);
     __syncthreads();
-    if (bact) F::inv_b(b, idx, Z0 + r * F::ZS, tw);
+    if (bact) F::inv_b_t(b, idx, Z0 + r * F::ZS, twB);
     __syncthreads();
     if constexpr (STAGE) mbar_wait(mb, 0, g.status);
     if (aact) {
@@ -521,7 +523,7 @@ __device__ __forceinline__ void row_rho_body(const Geo& g, const Ctx& ctx, float
             const int x = N2 * n1 + idx;
             a[n1] = make_float2(P[(2 * r) * N + x], P[(2 * r + 1) * N + x]);
         });
-        F::fwd_a(a, idx, Z1 + r * F::ZS, tw);
+        F::fwd_a_t(a, idx, Z1 + r * F::ZS, twA);
     }
     __syncthreads();
     finish_fwd<F>(Z1 + r * F::ZS, idx, pairok && idx < N1);
@@ -558,8 +560,9 @@ __global__ void __launch_bounds__(RR * Fft2<N1, N2>::T) kf_row_adj_rho(Geo g, fl
     using F = Fft2<N1, N2>;
     constexpr int N = F::N, T = F::T;
     extern __shared__ float2 sm[];
-    float2* tw = sm;
-    float2* Z0 = sm + N;
+    float2* twA = sm;       // twiddles of the A-layout step [N], read with consecutive n2 across threads
+    float2* twB = sm + N;   // twiddles of the B-layout step [N], read with consecutive k1 across threads
+    float2* Z0 = sm + 2 * N;
     float2* Z1 = Z0 + RR * F::ZS;
     float* PB = reinterpret_cast<float*>(Z1 + RR * F::ZS);   // [RR][N]
     float* Sx = PB + RR * N;                                 // staged rb_x, rb_y, c, p history [RR][N] each
@@ -614,7 +617,7 @@ __global__ void __launch_bounds__(RR * Fft2<N1, N2>::T) kf_row_adj_rho(Geo g, fl
         });
     }
     const float acy = g.a_cell[yy];
-    for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = g.tw[i];
+    F::fill_tables(twA, twB, g.tw, threadIdx.x, blockDim.x);
     if (first)
         for (int i = threadIdx.x; i < RR * N; i += blockDim.x) PB[i] = 0.f;
     pdl_wait_then_release();
@@ -634,7 +637,7 @@ __global__ void __launch_bounds__(RR * Fft2<N1, N2>::T) kf_row_adj_rho(Geo g, fl
         load_c2r_b<F>(b, idx, q0, q0 + g.hp);
     }
     __syncthreads();
-    if (bact) F::inv_b(b, idx, Z0 + r * F::ZS, tw);
+    if (bact) F::inv_b_t(b, idx, Z0 + r * F::ZS, twB);
     __syncthreads();
     if (!first && pairok && idx < N2) {
         float2 a[N1];
@@ -694,7 +697,7 @@ __global__ void __launch_bounds__(RR * Fft2<N1, N2>::T) kf_row_adj_rho(Geo g, fl
             by[x] = acy * ty;
             a[n1] = make_float2(tx, ty);
         });
-        F::fwd_a(a, idx, Z1 + r * F::ZS, tw);
+        F::fwd_a_t(a, idx, Z1 + r * F::ZS, twA);
     }
     __syncthreads();
     finish_fwd<F>(Z1 + r * F::ZS, idx, rowok && idx < N1);

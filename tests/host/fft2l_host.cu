@@ -12,6 +12,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstdint>
+#include <cstdlib>
 #include <vector>
 
 #include "fft2l.cuh"
@@ -57,6 +58,38 @@ void run_case(const std::vector<float2>& x) {
         F::inv_a_load(a, n2, Z.data());
         F::inv_a(a);
         for (int n1 = 0; n1 < N1; ++n1) y[n2 + N2 * n1] = a[n1];
+    }
+    // the same transforms with the per-layout twiddle tables of the row passes: bitwise equal
+    {
+        std::vector<float2> twA(N), twB(N), Z2(F::ZS), X2(N), y2(N);
+        F::fill_tables(twA.data(), twB.data(), tw.data(), 0, 1);
+        for (int n2 = 0; n2 < N2; ++n2) {
+            float2 a[N1];
+            for (int n1 = 0; n1 < N1; ++n1) a[n1] = x[N2 * n1 + n2];
+            F::fwd_a_t(a, n2, Z2.data(), twA.data());
+        }
+        for (int k1 = 0; k1 < N1; ++k1) {
+            float2 b[N2];
+            F::fwd_b_load(b, k1, Z2.data());
+            F::fwd_b(b);
+            for (int k2 = 0; k2 < N2; ++k2) X2[k1 + N1 * k2] = b[k2];
+        }
+        for (int k1 = 0; k1 < N1; ++k1) {
+            float2 b[N2];
+            for (int k2 = 0; k2 < N2; ++k2) b[k2] = X[k1 + N1 * k2];
+            F::inv_b_t(b, k1, Z2.data(), twB.data());
+        }
+        for (int n2 = 0; n2 < N2; ++n2) {
+            float2 a[N1];
+            F::inv_a_load(a, n2, Z2.data());
+            F::inv_a(a);
+            for (int n1 = 0; n1 < N1; ++n1) y2[n2 + N2 * n1] = a[n1];
+        }
+        for (int i = 0; i < N; ++i)
+            if (X2[i].x != X[i].x || X2[i].y != X[i].y || y2[i].x != y[i].x || y2[i].y != y[i].y) {
+                std::fprintf(stderr, "table-order twiddles differ at %d (N1=%d N2=%d)\n", i, N1, N2);
+                std::exit(3);
+            }
     }
     float2 d[N1], e[N2];
     for (int i = 0; i < N1; ++i) d[i] = x[i];
