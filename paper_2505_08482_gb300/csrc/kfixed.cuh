@@ -214,12 +214,12 @@ __global__ void __launch_bounds__(2 * CC * Fft2<N1, N2>::T) kf_col(Geo g, float2
 
 // Split the natural-order spectra W[j] (of a_j + i b_j) of nseq rows into half spectra:
 // a_j -> row rowa(j), b_j -> row rowb(j).
-template <class F, class RowA, class RowB>
+template <class F, int ZR, class RowA, class RowB>
 __device__ __forceinline__ void unpack_rows(const float2* Z, int nseq, RowA rowa, RowB rowb) {
     constexpr int H = F::N / 2 + 1;
     for (int i = threadIdx.x; i < nseq * H; i += blockDim.x) {
         const int j = i / H, kx = i - j * H;
-        const float2* W = Z + j * F::ZS;
+        const float2* W = Z + j * ZR;
         const float2 zk = W[kx];
         const float2 zm = W[kx == 0 ? 0 : F::N - kx];
         rowa(j)[kx] = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
@@ -241,12 +241,33 @@ __device__ __forceinline__ void finish_fwd(float2* Zs, int idx, bool active) {
     __syncthreads();
 }
 
+// Row strides (elements) of the row passes' shared buffers: zs for a transpose buffer (float2),
+// pn for a real row (float).  The unpadded strides (the Fft2 buffer size, the row length) put
+// rows that share a warp on the same banks; these were chosen by counting the shared-memory
+// wavefronts of the passes' main patterns (A- and B-layout steps, row stores, pair loads) for
+// tiles of 4 and 8 rows, and never raise the count.
+template <int N1, int N2>
+struct RowPad {
+    static constexpr int zs = Fft2<N1, N2>::ZS, pn = N1 * N2;
+};
+template <> struct RowPad<9, 12> { static constexpr int zs = 124, pn = 108; };
+template <> struct RowPad<12, 9> { static constexpr int zs = 108, pn = 117; };
+template <> struct RowPad<12, 12> { static constexpr int zs = 156, pn = 172; };
+template <> struct RowPad<12, 15> { static constexpr int zs = 180, pn = 207; };
+template <> struct RowPad<15, 12> { static constexpr int zs = 204, pn = 182; };
+template <> struct RowPad<10, 20> { static constexpr int zs = 212, pn = 202; };
+template <> struct RowPad<20, 10> { static constexpr int zs = 220, pn = 202; };
+template <> struct RowPad<15, 20> { static constexpr int zs = 324, pn = 314; };
+template <> struct RowPad<20, 15> { static constexpr int zs = 300, pn = 312; };
+
 // Shared memory of the row passes: the two twiddle tables, two transpose buffers and RR real rows
 // (base); staged: then ns arrays of RR rows, the PML factors, nc arrays of RR domain
 // rows of width n, and the mbarrier.
 template <class F, int RR>
 struct RowSmem {
-    static constexpr size_t base = (2 * F::N + 2 * RR * F::ZS) * sizeof(float2) + RR * F::N * sizeof(float);
+    static constexpr int ZR = RowPad<F::N1, F::N2>::zs, PN = RowPad<F::N1, F::N2>::pn;
+    static_assert(ZR >= F::ZS && PN >= F::N, "padded strides");
+    static constexpr size_t base = (2 * F::N + 2 * RR * ZR) * sizeof(float2) + RR * PN * sizeof(float);
     static constexpr size_t staged(int ns, int nc, int n) {
         return base + (size_t(ns) * RR + 1) * F::N * sizeof(float) + size_t(nc) * RR * n * sizeof(float) + 16;
     }
@@ -268,12 +289,13 @@ __device__ __forceinline__ void row_u_body(const Geo& g, const Ctx& ctx, float2*
                                            int kind, int init) {
     using F = Fft2<N1, N2>;
     constexpr int N = F::N, T = F::T;
+    constexpr int ZR = RowPad<N1, N2>::zs, PN = RowPad<N1, N2>::pn;   // padded row strides
     extern __shared__ float2 sm[];
     float2* twA = sm;       // twiddles of the A-layout step [N], read with consecutive n2 across threads
     float2* twB = sm + N;   // twiddles of the B-layout step [N], read with consecutive k1 across threads
     float2* Z0 = sm + 2 * N;
-    float2* Z1 = Z0 + RR * F::ZS;
-    float* Sx = reinterpret_cast<float*>(Z1 + RR * F::ZS) + RR * N;   // staged u_x, u_y [RR][N] (after base)
+    float2* Z1 = Z0 + RR * ZR;
+    float* Sx = reinterpret_cast<float*>(Z1 + RR * ZR) + RR * PN;   // staged u_x, u_y [RR][N] (after base)
     float* Sy = Sx + RR * N;
     float* Sa = Sy + RR * N;                                           // PML factors [N]
     uint64_t* mb = reinterpret_cast<uint64_t*>(Sa + N);
@@ -316,12 +338,12 @@ __device__ __forceinline__ void row_u_body(const Geo& g, const Ctx& ctx, float2*
     float2 b[N2];
     if (bact) load_c2r_b<F>(b, idx, A + row * g.hp, B + row * g.hp);
     __syncthreads();
-    if (bact) F::inv_b_t(b, idx, Z0 + r * F::ZS, twB);
+    if (bact) F::inv_b_t(b, idx, Z0 + r * ZR, twB);
     __syncthreads();
     if constexpr (STAGE) mbar_wait(mb, 0, g.status);
     if (aact) {
         float2 a[N1];
-        F::inv_a_load(a, idx, Z0 + r * F::ZS);
+        F::inv_a_load(a, idx, Z0 + r * ZR);
         F::inv_a(a);
         static_for<0, N1>([&](auto I) {
             constexpr int n1 = decltype(I)::value;
@@ -362,11 +384,11 @@ __device__ __forceinline__ void row_u_body(const Geo& g, const Ctx& ctx, float2*
                 a[n1] = make_float2(tpx, tpy);
             }
         });
-        F::fwd_a_t(a, idx, Z1 + r * F::ZS, twA);
+        F::fwd_a_t(a, idx, Z1 + r * ZR, twA);
     }
     __syncthreads();
-    finish_fwd<F>(Z1 + r * F::ZS, idx, bact);
-    unpack_rows<F>(Z1, nr, [&](int j) { return A + (size_t(k) * N + y0 + j) * g.hp; },
+    finish_fwd<F>(Z1 + r * ZR, idx, bact);
+    unpack_rows<F, ZR>(Z1, nr, [&](int j) { return A + (size_t(k) * N + y0 + j) * g.hp; },
                    [&](int j) { return B + (size_t(k) * N + y0 + j) * g.hp; });
 }
 
@@ -388,13 +410,14 @@ __device__ __forceinline__ void row_rho_body(const Geo& g, const Ctx& ctx, float
                                              float* __restrict__ hist, int hist_slot) {
     using F = Fft2<N1, N2>;
     constexpr int N = F::N, T = F::T;
+    constexpr int ZR = RowPad<N1, N2>::zs, PN = RowPad<N1, N2>::pn;   // padded row strides
     extern __shared__ float2 sm[];
     float2* twA = sm;       // twiddles of the A-layout step [N], read with consecutive n2 across threads
     float2* twB = sm + N;   // twiddles of the B-layout step [N], read with consecutive k1 across threads
     float2* Z0 = sm + 2 * N;
-    float2* Z1 = Z0 + RR * F::ZS;
-    float* P = reinterpret_cast<float*>(Z1 + RR * F::ZS);   // [RR][N]
-    float* Sx = P + RR * N;                                 // staged rho_x, rho_y, c [RR][N] each
+    float2* Z1 = Z0 + RR * ZR;
+    float* P = reinterpret_cast<float*>(Z1 + RR * ZR);   // [RR][PN]
+    float* Sx = P + RR * PN;                                // staged rho_x, rho_y, c [RR][N] each
     float* Sy = Sx + RR * N;
     float* Sc = Sy + RR * N;
     float* Sa = Sc + RR * N;                                // PML factors [N]
@@ -446,15 +469,15 @@ __device__ __forceinline__ void row_rho_body(const Geo& g, const Ctx& ctx, float
     float2 b[N2];
     if (bact) load_c2r_b<F>(b, idx, A + row * g.hp, B + row * g.hp);
     __syncthreads();
-    if (bact) F::inv_b_t(b, idx, Z0 + r * F::ZS, twB);
+    if (bact) F::inv_b_t(b, idx, Z0 + r * ZR, twB);
     __syncthreads();
     if constexpr (STAGE) mbar_wait(mb, 0, g.status);
     if (aact) {
-        float* Pr = P + r * N;
+        float* Pr = P + r * PN;
         float* hr = hist ? hist + (size_t(k) * g.s_eff + hist_slot) * N * N + size_t(yy) * N : nullptr;
         float2 a[N1];
         if (mode == 0) {
-            F::inv_a_load(a, idx, Z0 + r * F::ZS);
+            F::inv_a_load(a, idx, Z0 + r * ZR);
             F::inv_a(a);
         }
         static_for<0, N1>([&](auto I) {
@@ -509,7 +532,7 @@ __device__ __forceinline__ void row_rho_body(const Geo& g, const Ctx& ctx, float
             const int2 se = g.sent[e];
             const float4 sw = g.sentw[e];
             const int rr = int(sw.w) - y0;
-            const float v = sw.z * (sw.x * P[rr * N + se.y] + sw.y * P[rr * N + se.y + 1]);
+            const float v = sw.z * (sw.x * P[rr * PN + se.y] + sw.y * P[rr * PN + se.y + 1]);
             // at most two adds (rows iy, iy+1) onto a zeroed sample: order-independent
             atomicAdd(&y[(size_t(k) * g.nt + tstep) * g.m + se.x], v);
         }
@@ -521,13 +544,13 @@ __device__ __forceinline__ void row_rho_body(const Geo& g, const Ctx& ctx, float
         static_for<0, N1>([&](auto I) {
             constexpr int n1 = decltype(I)::value;
             const int x = N2 * n1 + idx;
-            a[n1] = make_float2(P[(2 * r) * N + x], P[(2 * r + 1) * N + x]);
+            a[n1] = make_float2(P[(2 * r) * PN + x], P[(2 * r + 1) * PN + x]);
         });
-        F::fwd_a_t(a, idx, Z1 + r * F::ZS, twA);
+        F::fwd_a_t(a, idx, Z1 + r * ZR, twA);
     }
     __syncthreads();
-    finish_fwd<F>(Z1 + r * F::ZS, idx, pairok && idx < N1);
-    unpack_rows<F>(Z1, np, [&](int j) { return A + (size_t(k) * N + y0 + 2 * j) * g.hp; },
+    finish_fwd<F>(Z1 + r * ZR, idx, pairok && idx < N1);
+    unpack_rows<F, ZR>(Z1, np, [&](int j) { return A + (size_t(k) * N + y0 + 2 * j) * g.hp; },
                    [&](int j) { return A + (size_t(k) * N + y0 + 2 * j + 1) * g.hp; });
 }
 
@@ -559,13 +582,14 @@ __global__ void __launch_bounds__(RR * Fft2<N1, N2>::T) kf_row_adj_rho(Geo g, fl
                                                                       int hist_slot) {
     using F = Fft2<N1, N2>;
     constexpr int N = F::N, T = F::T;
+    constexpr int ZR = RowPad<N1, N2>::zs, PN = RowPad<N1, N2>::pn;   // padded row strides
     extern __shared__ float2 sm[];
     float2* twA = sm;       // twiddles of the A-layout step [N], read with consecutive n2 across threads
     float2* twB = sm + N;   // twiddles of the B-layout step [N], read with consecutive k1 across threads
     float2* Z0 = sm + 2 * N;
-    float2* Z1 = Z0 + RR * F::ZS;
-    float* PB = reinterpret_cast<float*>(Z1 + RR * F::ZS);   // [RR][N]
-    float* Sx = PB + RR * N;                                 // staged rb_x, rb_y, c, p history [RR][N] each
+    float2* Z1 = Z0 + RR * ZR;
+    float* PB = reinterpret_cast<float*>(Z1 + RR * ZR);   // [RR][PN]
+    float* Sx = PB + RR * PN;                                // staged rb_x, rb_y, c, p history [RR][N] each
     float* Sy = Sx + RR * N;
     float* Sc = Sy + RR * N;
     float* Sh = Sc + RR * N;
@@ -619,7 +643,7 @@ __global__ void __launch_bounds__(RR * Fft2<N1, N2>::T) kf_row_adj_rho(Geo g, fl
     const float acy = g.a_cell[yy];
     F::fill_tables(twA, twB, g.tw, threadIdx.x, blockDim.x);
     if (first)
-        for (int i = threadIdx.x; i < RR * N; i += blockDim.x) PB[i] = 0.f;
+        for (int i = threadIdx.x; i < RR * PN; i += blockDim.x) PB[i] = 0.f;
     pdl_wait_then_release();
     const float* hr = hist + (size_t(k) * g.s_eff + hist_slot) * N * N + size_t(yy) * N;
     if constexpr (STAGE) {
@@ -637,17 +661,17 @@ __global__ void __launch_bounds__(RR * Fft2<N1, N2>::T) kf_row_adj_rho(Geo g, fl
         load_c2r_b<F>(b, idx, q0, q0 + g.hp);
     }
     __syncthreads();
-    if (bact) F::inv_b_t(b, idx, Z0 + r * F::ZS, twB);
+    if (bact) F::inv_b_t(b, idx, Z0 + r * ZR, twB);
     __syncthreads();
     if (!first && pairok && idx < N2) {
         float2 a[N1];
-        F::inv_a_load(a, idx, Z0 + r * F::ZS);
+        F::inv_a_load(a, idx, Z0 + r * ZR);
         F::inv_a(a);
         static_for<0, N1>([&](auto I) {
             constexpr int n1 = decltype(I)::value;
             const int x = idx + N2 * n1;
-            PB[(2 * r) * N + x] = a[n1].x;
-            PB[(2 * r + 1) * N + x] = a[n1].y;
+            PB[(2 * r) * PN + x] = a[n1].x;
+            PB[(2 * r + 1) * PN + x] = a[n1].y;
         });
     }
     __syncthreads();
@@ -658,8 +682,8 @@ __global__ void __launch_bounds__(RR * Fft2<N1, N2>::T) kf_row_adj_rho(Geo g, fl
             const int2 se = g.sent[e];
             const float4 sw = g.sentw[e];
             const float v = rv[se.x] * sw.z;
-            PB[rr * N + se.y] += sw.x * v;
-            PB[rr * N + se.y + 1] += sw.y * v;
+            PB[rr * PN + se.y] += sw.x * v;
+            PB[rr * PN + se.y + 1] += sw.y * v;
         }
     }
     __syncthreads();
@@ -687,7 +711,7 @@ __global__ void __launch_bounds__(RR * Fft2<N1, N2>::T) kf_row_adj_rho(Geo g, fl
                 cbo = cb[n1];
                 h = hv[n1];
             }
-            const float p_b = PB[r * N + x];
+            const float p_b = PB[r * PN + x];
             const float c2 = c * c;
             const float vbx = v0 + c2 * p_b;
             const float vby = v1 + c2 * p_b;
@@ -697,11 +721,11 @@ __global__ void __launch_bounds__(RR * Fft2<N1, N2>::T) kf_row_adj_rho(Geo g, fl
             by[x] = acy * ty;
             a[n1] = make_float2(tx, ty);
         });
-        F::fwd_a_t(a, idx, Z1 + r * F::ZS, twA);
+        F::fwd_a_t(a, idx, Z1 + r * ZR, twA);
     }
     __syncthreads();
-    finish_fwd<F>(Z1 + r * F::ZS, idx, rowok && idx < N1);
-    unpack_rows<F>(Z1, nr, [&](int j) { return A2 + (size_t(k) * N + y0 + j) * g.hp; },
+    finish_fwd<F>(Z1 + r * ZR, idx, rowok && idx < N1);
+    unpack_rows<F, ZR>(Z1, nr, [&](int j) { return A2 + (size_t(k) * N + y0 + j) * g.hp; },
                    [&](int j) { return B2 + (size_t(k) * N + y0 + j) * g.hp; });
 }
 
