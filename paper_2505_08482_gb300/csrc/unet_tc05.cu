@@ -33,16 +33,25 @@
 namespace pat {
 namespace tc05 {
 
-constexpr int BM = 128, BN = 128, BK = 64, STAGES = 4, THREADS = 128;
-constexpr uint32_t TILE = BM * BK * 2;              // bytes of one operand tile (A and B alike: BM == BN)
-constexpr size_t SMEM = 1024 + 2 * STAGES * TILE + 256;
+constexpr int BM = 128, BK = 64, STAGES = 4, THREADS = 128;
+constexpr uint32_t TILE_A = BM * BK * 2;            // bytes of one A tile (128 rows x 64 K-elements)
 constexpr uint64_t kWaitNs = 200000000ull;          // 0.2 s per wait
-static_assert(BM == BN, "one tile shape for both operands");
+constexpr int GROUP_M = 8;                          // tile rows per group of the tile order
+
+// Shared memory of a CTA with an N tile of BN: the 4-stage ring of A and B tiles (1024-byte
+// aligned for the 128-byte swizzle) and the barriers.
+template <int BN>
+__host__ __device__ constexpr size_t smem_bytes() {
+    return 1024 + size_t(STAGES) * (TILE_A + uint32_t(BN) * BK * 2) + 256;
+}
 
 // Instruction descriptor of kind::f16: FP32 accumulator (bits 4-5 = 1), A and B BF16
 // (bits 7-9 = 1, 10-12 = 1), both K-major (bits 15, 16 = 0), N / 8 at bits 17-22,
 // M / 16 at bits 24-28.
-constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(BN >> 3) << 17) | (uint32_t(BM >> 4) << 24);
+template <int BN>
+__host__ __device__ constexpr uint32_t idesc() {
+    return (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(BN >> 3) << 17) | (uint32_t(BM >> 4) << 24);
+}
 
 // Shared-memory matrix descriptor of a K-major tile with the 128-byte swizzle: start
 // address / 16 (bits 0-13), leading byte offset / 16 (bits 16-29; not used by swizzled
@@ -61,11 +70,11 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, i
         : "memory");
 }
 
-__device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t da, uint64_t db, uint32_t acc) {
+__device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t da, uint64_t db, uint32_t id, uint32_t acc) {
     asm volatile(
         "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
         "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
-        "l"(da), "l"(db), "r"(kIdesc), "r"(acc)
+        "l"(da), "l"(db), "r"(id), "r"(acc)
         : "memory");
 }
 
@@ -89,20 +98,29 @@ struct Args {
     int* status;           // device status word (bit PAT_STATUS_TC05 on a given-up wait), or null
 };
 
+// grid.x: output tiles in groups of GROUP_M tile rows (within a group the tile row varies
+// fastest, so that CTAs running at the same time share A and B tiles in L2); grid.z: K split.
+template <int BN>
 __global__ void __launch_bounds__(THREADS, 1) k_gemm_tc05(const __grid_constant__ CUtensorMap ta,
                                                           const __grid_constant__ CUtensorMap tb, Args a) {
+    constexpr uint32_t TILE_B = uint32_t(BN) * BK * 2;
     extern __shared__ unsigned char smraw[];
     unsigned char* sm = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~uintptr_t(1023));
     unsigned char* sA = sm;
-    unsigned char* sB = sm + STAGES * TILE;
-    uint64_t* full = reinterpret_cast<uint64_t*>(sm + 2 * STAGES * TILE);
+    unsigned char* sB = sm + STAGES * TILE_A;
+    uint64_t* full = reinterpret_cast<uint64_t*>(sB + STAGES * TILE_B);
     uint64_t* empty = full + STAGES;
     uint64_t* done = empty + STAGES;
     uint32_t* tslot = reinterpret_cast<uint32_t*>(done + 1);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tslot + 1);
     int* issued = const_cast<int*>(abort_flag) + 1;   // copies issued by the producer
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+    const int tiles_m = (a.M + BM - 1) / BM, tiles_n = (a.N + BN - 1) / BN;
+    const int t = blockIdx.x;
+    const int first_m = (t / (GROUP_M * tiles_n)) * GROUP_M;
+    const int gsize = min(GROUP_M, tiles_m - first_m);
+    const int in_group = t - first_m * tiles_n;
+    const int m0 = (first_m + in_group % gsize) * BM, n0 = (in_group / gsize) * BN;
     const int kb = blockIdx.z * a.ksplit;
     const int ke = min(a.K, kb + a.ksplit);
     const int nk = ke > kb ? (ke - kb + BK - 1) / BK : 0;
@@ -136,9 +154,9 @@ __global__ void __launch_bounds__(THREADS, 1) k_gemm_tc05(const __grid_constant_
                 break;
             }
             if (*abort_flag) break;
-            mbar_arrive_expect(full + s, 2 * TILE);
-            tma_load_2d(sA + s * TILE, &ta, kb + kt * BK, m0, full + s);
-            tma_load_2d(sB + s * TILE, &tb, kb + kt * BK, n0, full + s);
+            mbar_arrive_expect(full + s, TILE_A + TILE_B);
+            tma_load_2d(sA + s * TILE_A, &ta, kb + kt * BK, m0, full + s);
+            tma_load_2d(sB + s * TILE_B, &tb, kb + kt * BK, n0, full + s);
             *issued = kt + 1;
         }
     } else if (warp == 1 && lane == 0) {   // MMA issuer
@@ -149,10 +167,10 @@ __global__ void __launch_bounds__(THREADS, 1) k_gemm_tc05(const __grid_constant_
                 break;
             }
             fence_after();
-            const uint32_t a0 = s_addr(sA + s * TILE), b0 = s_addr(sB + s * TILE);
+            const uint32_t a0 = s_addr(sA + s * TILE_A), b0 = s_addr(sB + s * TILE_B);
 #pragma unroll
             for (int kk = 0; kk < BK / 16; ++kk)   // 16 K-elements = 32 bytes along the swizzled row
-                mma_bf16(tmem, desc_sw128(a0 + 32 * kk), desc_sw128(b0 + 32 * kk), (kt | kk) ? 1u : 0u);
+                mma_bf16(tmem, desc_sw128(a0 + 32 * kk), desc_sw128(b0 + 32 * kk), idesc<BN>(), (kt | kk) ? 1u : 0u);
             mma_commit(empty + s);
         }
         mma_commit(done);
@@ -226,8 +244,8 @@ PFN_cuTensorMapEncodeTiled_v12000 encoder() {
     return fn;
 }
 
-// 2-D tensor map of a row-major [rows][K] bf16 matrix with row pitch ld, boxes of BK x 128
-int make_map(CUtensorMap* m, const __nv_bfloat16* base, int rows, int K, int ld) {
+// 2-D tensor map of a row-major [rows][K] bf16 matrix with row pitch ld, boxes of BK x box_rows
+int make_map(CUtensorMap* m, const __nv_bfloat16* base, int rows, int K, int ld, int box_rows) {
     PFN_cuTensorMapEncodeTiled_v12000 enc = encoder();
     if (!enc) {
         set_error("unet_gemm_tc05: cuTensorMapEncodeTiled is not available from the driver");
@@ -235,7 +253,7 @@ int make_map(CUtensorMap* m, const __nv_bfloat16* base, int rows, int K, int ld)
     }
     const cuuint64_t dims[2] = {cuuint64_t(K), cuuint64_t(rows)};
     const cuuint64_t strides[1] = {cuuint64_t(ld) * 2};
-    const cuuint32_t box[2] = {cuuint32_t(BK), cuuint32_t(BM)};
+    const cuuint32_t box[2] = {cuuint32_t(BK), cuuint32_t(box_rows)};
     const cuuint32_t es[2] = {1, 1};
     const CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<__nv_bfloat16*>(base), dims, strides,
                            box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
@@ -246,6 +264,30 @@ int make_map(CUtensorMap* m, const __nv_bfloat16* base, int rows, int K, int ld)
         return PAT_ECUDA;
     }
     return PAT_OK;
+}
+
+template <int BN>
+int launch(cudaStream_t st, const __nv_bfloat16* A, int lda, const __nv_bfloat16* B, int ldb, Args a) {
+    static bool configured = false;
+    if (!configured) {
+        PAT_CUDA(cudaFuncSetAttribute(k_gemm_tc05<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      int(smem_bytes<BN>())));
+        configured = true;
+    }
+    CUtensorMap ta, tb;
+    int rc = make_map(&ta, A, a.M, a.K, lda, BM);
+    if (rc == PAT_OK) rc = make_map(&tb, B, a.N, a.K, ldb, BN);
+    if (rc != PAT_OK) return rc;
+    const long long tiles = (long long)((a.M + BM - 1) / BM) * ((a.N + BN - 1) / BN);
+    const int nz = (a.K + a.ksplit - 1) / a.ksplit;
+    if (tiles > 2147483647LL || nz > 65535) {
+        set_error("unet_gemm_tc05: too many tiles (M=%d N=%d, split %d)", a.M, a.N, nz);
+        return PAT_EINVAL;
+    }
+    count_launch();
+    k_gemm_tc05<BN><<<dim3(unsigned(tiles), 1, nz), THREADS, smem_bytes<BN>(), st>>>(ta, tb, a);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? PAT_OK : cuda_fail(e, "k_gemm_tc05");
 }
 
 }  // namespace tc05
@@ -263,30 +305,12 @@ int unet_gemm_tc05(cudaStream_t st, const __nv_bfloat16* A, int lda, const __nv_
         set_error("unet_gemm_tc05: unsupported operands (M=%d N=%d K=%d lda=%d ldb=%d)", M, N, K, lda, ldb);
         return PAT_EINVAL;
     }
-    static bool configured = false;
-    if (!configured) {
-        PAT_CUDA(cudaFuncSetAttribute(tc05::k_gemm_tc05, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      int(tc05::SMEM)));
-        configured = true;
-    }
-    CUtensorMap ta, tb;
-    int rc = tc05::make_map(&ta, A, M, K, lda);
-    if (rc == PAT_OK) rc = tc05::make_map(&tb, B, N, K, ldb);
-    if (rc != PAT_OK) return rc;
     splitk = std::max(1, splitk);
     int ks = (K + splitk - 1) / splitk;
     ks = (ks + tc05::BK - 1) / tc05::BK * tc05::BK;   // split boundaries on whole K boxes
-    const int nz = (K + ks - 1) / ks;
     tc05::Args a{M, N, K, ks, bias, relu, C, ldc, out_mode, d_status};
-    dim3 grid((N + tc05::BN - 1) / tc05::BN, (M + tc05::BM - 1) / tc05::BM, nz);
-    if (grid.y > 65535u || grid.z > 65535u) {
-        set_error("unet_gemm_tc05: grid too large (M=%d, split %d)", M, nz);
-        return PAT_EINVAL;
-    }
-    count_launch();
-    tc05::k_gemm_tc05<<<grid, tc05::THREADS, tc05::SMEM, st>>>(ta, tb, a);
-    cudaError_t e = cudaGetLastError();
-    return e == cudaSuccess ? PAT_OK : cuda_fail(e, "k_gemm_tc05");
+    // the wider N tile halves the A traffic per MMA where N allows it
+    return N >= 256 ? tc05::launch<256>(st, A, lda, B, ldb, a) : tc05::launch<128>(st, A, lda, B, ldb, a);
 }
 
 }  // namespace pat
