@@ -309,8 +309,14 @@ int unet_gemm_tc05(cudaStream_t st, const __nv_bfloat16* A, int lda, const __nv_
     int ks = (K + splitk - 1) / splitk;
     ks = (ks + tc05::BK - 1) / tc05::BK * tc05::BK;   // split boundaries on whole K boxes
     tc05::Args a{M, N, K, ks, bias, relu, C, ldc, out_mode, d_status};
-    // the wider N tile halves the A traffic per MMA where N allows it
-    return N >= 256 ? tc05::launch<256>(st, A, lda, B, ldb, a) : tc05::launch<128>(st, A, lda, B, ldb, a);
+    // the wider N tile halves the A traffic per MMA, where N allows it and the product still has
+    // at least two waves of tiles (fewer tiles would leave SMs idle)
+    int dev = 0, sms = 148;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const long long wide_tiles = (long long)((M + tc05::BM - 1) / tc05::BM) * ((N + 255) / 256) *
+                                 ((K + ks - 1) / ks);
+    return (N >= 256 && wide_tiles >= 2LL * sms) ? tc05::launch<256>(st, A, lda, B, ldb, a)
+                                                 : tc05::launch<128>(st, A, lda, B, ldb, a);
 }
 
 }  // namespace pat
