@@ -27,8 +27,9 @@ def _gemm(A, B, path, status=None):
     return C
 
 
+# the last shape has enough tiles for the 256-wide N tile (ragged in M, N and K)
 @pytest.mark.parametrize("M,N,K", [(128, 128, 64), (200, 72, 136), (1000, 256, 576), (4096, 32, 72),
-                                   (64, 300, 4608)])
+                                   (64, 300, 4608), (20000, 300, 136)])
 def test_tc05_gemm_matches_fp64_and_warp_path(M, N, K):
     g = torch.Generator().manual_seed(M + N + K)
     A = torch.randn((M, K), generator=g).to(torch.bfloat16).cuda()
