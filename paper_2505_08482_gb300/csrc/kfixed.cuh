@@ -644,6 +644,24 @@ __global__ void __launch_bounds__(RR * Fft2<N1, N2>::T) kf_row_adj_rho(Geo g, fl
     F::fill_tables(twA, twB, g.tw, threadIdx.x, blockDim.x);
     if (first)
         for (int i = threadIdx.x; i < RR * PN; i += blockDim.x) PB[i] = 0.f;
+    // The source S^T r^n of the tile's rows, fetched before the wait (the residual is written
+    // before the reverse sweep starts): per sensor entry its column and its two weighted values,
+    // so that the in-order accumulation after the inverse transform reads only shared memory.
+    constexpr int kMaxEnt = 16 * RR;
+    __shared__ int s_ecol[kMaxEnt];
+    __shared__ float s_ewa[kMaxEnt], s_ewb[kMaxEnt];
+    const int e0 = g.srow[y0], e1 = g.srow[y0 + nr];
+    const bool ent_pre = e1 - e0 <= kMaxEnt;
+    const float* rv = resid + (size_t(k) * g.nt + tstep) * g.m;
+    if (ent_pre)
+        for (int e = e0 + int(threadIdx.x); e < e1; e += blockDim.x) {
+            const int2 se = g.sent[e];
+            const float4 sw = g.sentw[e];
+            const float v = rv[se.x] * sw.z;
+            s_ecol[e - e0] = se.y;
+            s_ewa[e - e0] = sw.x * v;
+            s_ewb[e - e0] = sw.y * v;
+        }
     pdl_wait_then_release();
     const float* hr = hist + (size_t(k) * g.s_eff + hist_slot) * N * N + size_t(yy) * N;
     if constexpr (STAGE) {
@@ -677,13 +695,21 @@ __global__ void __launch_bounds__(RR * Fft2<N1, N2>::T) kf_row_adj_rho(Geo g, fl
     __syncthreads();
     if (threadIdx.x < nr) {   // S^T r^n, one thread per row: fixed order
         const int rr = threadIdx.x, yr = y0 + rr;
-        const float* rv = resid + (size_t(k) * g.nt + tstep) * g.m;
-        for (int e = g.srow[yr]; e < g.srow[yr + 1]; ++e) {
-            const int2 se = g.sent[e];
-            const float4 sw = g.sentw[e];
-            const float v = rv[se.x] * sw.z;
-            PB[rr * PN + se.y] += sw.x * v;
-            PB[rr * PN + se.y + 1] += sw.y * v;
+        const int ea = g.srow[yr], eb = g.srow[yr + 1];
+        if (ent_pre) {
+            for (int e = ea; e < eb; ++e) {
+                const int col = s_ecol[e - e0];
+                PB[rr * PN + col] += s_ewa[e - e0];
+                PB[rr * PN + col + 1] += s_ewb[e - e0];
+            }
+        } else {
+            for (int e = ea; e < eb; ++e) {
+                const int2 se = g.sent[e];
+                const float4 sw = g.sentw[e];
+                const float v = rv[se.x] * sw.z;
+                PB[rr * PN + se.y] += sw.x * v;
+                PB[rr * PN + se.y + 1] += sw.y * v;
+            }
         }
     }
     __syncthreads();
