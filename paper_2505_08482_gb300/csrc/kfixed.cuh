@@ -393,7 +393,7 @@ __device__ __forceinline__ void row_u_body(const Geo& g, const Ctx& ctx, float2*
 }
 
 template <int N1, int N2, int RR, bool STAGE>
-__global__ void __launch_bounds__(RR * Fft2<N1, N2>::T) kf_row_u(Geo g, float2* __restrict__ A,
+__global__ void __launch_bounds__(RR * Fft2<N1, N2>::T, RR >= 8 ? 3 : 1) kf_row_u(Geo g, float2* __restrict__ A,
                                                                 float2* __restrict__ B, float* __restrict__ ux,
                                                                 float* __restrict__ uy, int kind, int init) {
     row_u_body<N1, N2, RR, STAGE, false>(g, LaunchedCtx{int(blockIdx.x), int(blockIdx.y)}, A, B, ux, uy, kind, init);
@@ -566,7 +566,7 @@ __device__ __forceinline__ void row_rho_body(const Geo& g, const Ctx& ctx, float
 }
 
 template <int N1, int N2, int RR, bool STAGE>
-__global__ void __launch_bounds__(RR * Fft2<N1, N2>::T) kf_row_rho(Geo g, float2* __restrict__ A,
+__global__ void __launch_bounds__(RR * Fft2<N1, N2>::T, RR >= 8 ? 3 : 1) kf_row_rho(Geo g, float2* __restrict__ A,
                                                                   const float2* __restrict__ B,
                                                                   float* __restrict__ rx, float* __restrict__ ry,
                                                                   const float* __restrict__ cg, int mode,
