@@ -393,7 +393,7 @@ __device__ __forceinline__ void row_u_body(const Geo& g, const Ctx& ctx, float2*
 }
 
 template <int N1, int N2, int RR, bool STAGE>
-__global__ void __launch_bounds__(RR * Fft2<N1, N2>::T, RR >= 8 ? 3 : 1) kf_row_u(Geo g, float2* __restrict__ A,
+__global__ void __launch_bounds__(RR * Fft2<N1, N2>::T) kf_row_u(Geo g, float2* __restrict__ A,
                                                                 float2* __restrict__ B, float* __restrict__ ux,
                                                                 float* __restrict__ uy, int kind, int init) {
     row_u_body<N1, N2, RR, STAGE, false>(g, LaunchedCtx{int(blockIdx.x), int(blockIdx.y)}, A, B, ux, uy, kind, init);
@@ -566,7 +566,7 @@ __device__ __forceinline__ void row_rho_body(const Geo& g, const Ctx& ctx, float
 }
 
 template <int N1, int N2, int RR, bool STAGE>
-__global__ void __launch_bounds__(RR * Fft2<N1, N2>::T, RR >= 8 ? 3 : 1) kf_row_rho(Geo g, float2* __restrict__ A,
+__global__ void __launch_bounds__(RR * Fft2<N1, N2>::T) kf_row_rho(Geo g, float2* __restrict__ A,
                                                                   const float2* __restrict__ B,
                                                                   float* __restrict__ rx, float* __restrict__ ry,
                                                                   const float* __restrict__ cg, int mode,
@@ -579,8 +579,8 @@ __global__ void __launch_bounds__(RR * Fft2<N1, N2>::T, RR >= 8 ? 3 : 1) kf_row_
 
 // adjoint density row pass: pb = C2R(Q) + S^T r^n; rb += c^2 pb; cbar += 2 p pb / c;
 // t = a rb; rb <- a t; (A2, B2) <- R2C(t_x, t_y).  Adjoint state, dJ/dc accumulator,
-// medium and PML are fetched before the wait; the spectrum and the pressure history (the
-// segment recompute that writes it may be the preceding kernel) after it.
+// medium, PML, pressure history and sensor source are fetched before the wait; the spectrum,
+// written by the preceding kernel, after it.
 template <int N1, int N2, int RR, bool STAGE>
 __global__ void __launch_bounds__(RR * Fft2<N1, N2>::T) kf_row_adj_rho(Geo g, float2* __restrict__ A2,
                                                                       float2* __restrict__ B2,
@@ -631,7 +631,7 @@ __global__ void __launch_bounds__(RR * Fft2<N1, N2>::T) kf_row_adj_rho(Geo g, fl
             const size_t r0 = (size_t(k) * N + y0) * N;
             const uint32_t bytes = rows_bytes<N>(nr);
             const uint32_t cbytes = (cb_staged && d1 > d0) ? uint32_t(d1 - d0) * g.n * sizeof(float) : 0u;
-            mbar_init(mb, 2);   // this arrival and the history's after the wait
+            mbar_init(mb, 2);   // this arrival and the history's
             mbar_arrive_expect(mb, 3u * bytes + uint32_t(N * sizeof(float)) + cbytes);
             bulk_load(Sx, rbx + r0, bytes, mb);
             bulk_load(Sy, rby + r0, bytes, mb);
@@ -673,7 +673,9 @@ __global__ void __launch_bounds__(RR * Fft2<N1, N2>::T) kf_row_adj_rho(Geo g, fl
             s_ewa[e - e0] = sw.x * v;
             s_ewb[e - e0] = sw.y * v;
         }
-    pdl_wait_then_release();
+    // The pressure history is written by the segment recompute on the other stream, which this
+    // segment's first kernel waits for through an event (a full dependency), or by the forward
+    // sweep: never by the kernel just before, so it is fetched before the wait as well.
     const float* hr = hist + (size_t(k) * g.s_eff + hist_slot) * N * N + size_t(yy) * N;
     if constexpr (STAGE) {
         if (threadIdx.x == 0) {
@@ -684,6 +686,7 @@ __global__ void __launch_bounds__(RR * Fft2<N1, N2>::T) kf_row_adj_rho(Geo g, fl
     } else if (aact) {
         static_for<0, N1>([&](auto I) { hv[decltype(I)::value] = hr[idx + N2 * decltype(I)::value]; });
     }
+    pdl_wait_then_release();
     float2 b[N2];
     if (bact) {
         const float2* q0 = A2 + (size_t(k) * N + y0 + 2 * r) * g.hp;
