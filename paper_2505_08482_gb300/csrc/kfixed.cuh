@@ -465,17 +465,6 @@ __device__ __forceinline__ void row_rho_body(const Geo& g, const Ctx& ctx, float
     }
     const float acy = g.a_cell[yy];
     F::fill_tables(twA, twB, g.tw, threadIdx.x, blockDim.x);
-    // the tile's sensor entries (constant tables), staged in shared memory before the wait so that
-    // the gather after the update reads no global memory
-    constexpr int kMaxGat = 16 * RR;
-    __shared__ int2 s_gse[kMaxGat];
-    __shared__ float4 s_gsw[kMaxGat];
-    const int ge0 = g.srow[y0], ge1 = g.srow[y0 + nr];
-    if (y)
-        for (int e = ge0 + int(threadIdx.x); e < ge1 && e - ge0 < kMaxGat; e += blockDim.x) {
-            s_gse[e - ge0] = g.sent[e];
-            s_gsw[e - ge0] = g.sentw[e];
-        }
     ctx.input_ready();
     float2 b[N2];
     if (bact) load_c2r_b<F>(b, idx, A + row * g.hp, B + row * g.hp);
@@ -538,10 +527,10 @@ __device__ __forceinline__ void row_rho_body(const Geo& g, const Ctx& ctx, float
     }
     __syncthreads();
     if (y) {
-        for (int e = ge0 + int(threadIdx.x); e < ge1; e += blockDim.x) {
-            const bool st = e - ge0 < kMaxGat;
-            const int2 se = st ? s_gse[e - ge0] : g.sent[e];
-            const float4 sw = st ? s_gsw[e - ge0] : g.sentw[e];
+        const int e0 = g.srow[y0], e1 = g.srow[y0 + nr];
+        for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+            const int2 se = g.sent[e];
+            const float4 sw = g.sentw[e];
             const int rr = int(sw.w) - y0;
             const float v = sw.z * (sw.x * P[rr * PN + se.y] + sw.y * P[rr * PN + se.y + 1]);
             // at most two adds (rows iy, iy+1) onto a zeroed sample: order-independent
