@@ -83,3 +83,34 @@ def test_forward_is_linear_in_p0_and_deterministic():
     assert np.array_equal(y1, y2)
     y3 = plan.forward(_dev(c), _dev(2.0 * p0)).cpu().numpy()
     assert rel_l2(y3, 2.0 * y1) <= 1e-6
+
+
+def test_largest_grid_side():
+    """The largest supported FFT grid (Ng = 1024 = 984 + 2 x 20, generic passes) against the
+    oracle, forward and gradient; one more cell per side (Ng 1026) is rejected."""
+    from oracle.adjoint import adjoint_grad
+    from oracle.sensors import sensor_matrix
+    from paper_2505_08482_gb300 import _binding as B
+    n, K, nt = 984, 1, 16
+    rng = ps.rng_for(984)
+    c = 1500.0 + 60.0 * rng.uniform(size=(n, n))
+    p0 = np.zeros((K, n, n))
+    p0[0, 480:504, 480:504] = 1.0
+    xy = ps.rng_for(985).uniform(470, 514, size=(24, 2)) * 1e-4
+    gp = grid_params(n, nt, pml=20)
+    plan = gpu_plan(gp, xy, K, ckpt_every=8)
+    assert plan.ng == 1024 and plan.variants == 0
+    y = plan.forward(_dev(c), _dev(p0)).cpu().numpy()
+    g = oracle_grid(gp)
+    S = sensor_matrix(g, xy)
+    ref = _oracle_traces(gp, c, p0, xy)
+    assert rel_l2(y, ref) <= 1e-4
+    ym = ref + 0.01 * np.abs(ref).max() * ps.rng_for(986).standard_normal(ref.shape)
+    w = np.array([1.0 / np.abs(ref).max() ** 2])
+    J, gp0, gc = plan.adjoint_grad(_dev(np.full((n, n), 1500.0)), _dev(0.5 * p0), _dev(ym), _dev(w))
+    Jo, gpo, gco = adjoint_grad(g, np.full((n, n), 1500.0), 0.5 * p0, S, ym, w)
+    assert abs(J.item() - Jo) <= 1e-4 * Jo
+    assert rel_l2(gp0.cpu().numpy(), gpo) <= 1e-3
+    assert rel_l2(gc.cpu().numpy(), gco) <= 1e-3
+    with pytest.raises(B.PatError):
+        gpu_plan(grid_params(986, nt, pml=20), xy, K)

@@ -49,7 +49,7 @@ def test_forward_all_variants(n):
         assert rel_l2(outs[v], outs[-1]) <= 1e-5, v
 
 
-@pytest.mark.parametrize("n", [64, 160, 256])
+@pytest.mark.parametrize("n", sorted(SIDES))
 def test_gradient_all_variants(n):
     from oracle.adjoint import adjoint_grad
     from oracle.forward import forward
