@@ -20,6 +20,13 @@
 // registers (STAGE = false) or, with STAGE = true, by TMA bulk copies into
 // shared memory (the RR rows of a data set are contiguous: one copy per array),
 // which leaves the registers to the FFT so that more CTAs share an SM.
+//
+// In shared memory the row passes keep their twiddles in two per-layout tables (the threads of
+// one transform step read consecutive entries) and pad the row strides of their transpose
+// buffers and real rows (RowPad), so that rows sharing a warp fall on different banks.
+//
+// The same pass bodies also run inside the persistent forward sweep (PersistentImpl at the end
+// of this file), which takes their tiles from a work queue instead of a launch grid.
 #pragma once
 
 #include <cuda_runtime.h>
