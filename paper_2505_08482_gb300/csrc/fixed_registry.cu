@@ -1,5 +1,5 @@
-// Registry of the fixed-size passes: grid sides with a compiled two-level FFT.
-#include "kfixed.cuh"
+// Registry of the fixed-size passes: grid sides with compiled register FFTs.
+#include "kcluster.cuh"
 
 namespace pat {
 
@@ -15,6 +15,9 @@ const SweepOps* sweep_ops_180();
 const SweepOps* sweep_ops_200();
 const SweepOps* sweep_ops_240();
 const SweepOps* sweep_ops_300();
+const ClusterOps* cluster_ops_300();
+
+const ClusterOps* cluster_ops_for(int ng) { return ng == 300 ? cluster_ops_300() : nullptr; }
 
 const FixedOps* fixed_ops_for(int ng, int v) {
     switch (ng) {
@@ -40,6 +43,10 @@ const SweepOps* sweep_ops_for(int ng) {
     }
 }
 
-int fixed_variants(int ng) { return fixed_ops_for(ng, 0) ? 7 : 0; }
+int fixed_variants(int ng) {
+    int v = 0;
+    while (fixed_ops_for(ng, v)) ++v;
+    return v;
+}
 
 }  // namespace pat

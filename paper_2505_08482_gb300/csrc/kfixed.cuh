@@ -219,6 +219,102 @@ __global__ void __launch_bounds__(2 * CC * Fft2<N1, N2>::T) kf_col(Geo g, float2
     col_body<N1, N2, CC>(g, LaunchedCtx{int(blockIdx.x), int(blockIdx.y)}, A, B, mode, op, scale);
 }
 
+// Column pass on the three-level transform (Fft3): the same modes and multipliers as col_body,
+// with three times as many threads per column (every thread holds at most max(NA, NM, NB)
+// values), so that a launch at K = 8 keeps about three times as many warps on each SM.
+// Shared buffers per field: Z1 (A -> M forward, B -> M inverse), Z2 (M -> B forward, M -> A
+// inverse); the f = 1 threads of mode 0 read the f = 0 threads' M -> B buffer.
+template <int NA, int NM, int NB, int CC, class Ctx>
+__device__ __forceinline__ void col3_body(const Geo& g, const Ctx& ctx, float2* __restrict__ A,
+                                          float2* __restrict__ B, int mode, int op, float scale) {
+    using F = Fft3<NA, NM, NB>;
+    ctx.state_ready();
+    constexpr int N = F::N, T = F::T, ZS = F::ZS;
+    constexpr int NT = 2 * CC * T;
+    extern __shared__ float2 sm[];
+    float2* twA = sm;                       // [N]
+    float2* twM = twA + N;                  // [N2]
+    float2* MX = twM + F::N2;               // [N][CC] x multiplier at (ky, c)
+    float2* MY = MX + N * CC;               // [N][CC]
+    float2* Z1 = MY + N * CC;               // [2][ZS][CC]
+    float2* Z2 = Z1 + 2 * ZS * CC;          // [2][ZS][CC]
+    const int k = ctx.k;
+    const int f = threadIdx.x / (CC * T);
+    const int tl = threadIdx.x - f * (CC * T);
+    const int c = tl % CC, idx = tl / CC;
+    const int kx = ctx.bx * CC + c;
+    const bool colok = kx < g.hc;
+    const int kxc = colok ? kx : g.hc - 1;
+    const size_t base = size_t(k) * N * g.hp + kxc;
+    F::fill_tables(twA, twM, g.tw, threadIdx.x, NT);
+    for (int i = threadIdx.x; i < N * CC; i += NT) {
+        const int cc = i % CC, ky = i / CC;
+        const int kxs = min(ctx.bx * CC + cc, g.hc - 1);
+        float2 mx, my;
+        col_mults(g, kxs, ky, op, scale, mx, my);
+        MX[i] = mx;
+        MY[i] = my;
+    }
+    ctx.input_ready();
+    float2* Z1f = Z1 + f * ZS * CC + c;
+    float2* Z2f = Z2 + f * ZS * CC + c;
+    const bool own_fwd = mode != 0 || f == 0;
+    float2 a[NA];
+    if (idx < F::AT && own_fwd) {
+        const float2* src = (mode == 0 || f == 0) ? A : B;
+        static_for<0, NA>([&](auto I) {
+            constexpr int n1 = decltype(I)::value;
+            a[n1] = ld_spec(src + base + size_t(F::AT * n1 + idx) * g.hp);
+        });
+    }
+    __syncthreads();   // twiddles and multipliers staged by all threads
+    if (idx < F::AT && own_fwd) F::template fwd_a_t<CC>(a, idx, Z1f, twA);
+    __syncthreads();
+    if (idx < F::MT && own_fwd) F::template fwd_m<CC>(idx, Z1f, Z2f, twM);
+    __syncthreads();
+    float2 b[NB];
+    const float2* Mm = (f == 0) ? MX : MY;
+    float2* Zh = Z1 + ZS * CC + c;   // mode 2: the f = 1 product handed to the f = 0 thread
+    if (idx < F::BT) {
+        F::template fwd_b_load<CC>(b, idx, own_fwd ? Z2f : Z2 + c);
+        F::fwd_b(b);
+        static_for<0, NB>([&](auto I) {
+            constexpr int k2 = decltype(I)::value;
+            b[k2] = cmul(b[k2], Mm[(idx + F::BT * k2) * CC + c]);
+        });
+        if (mode == 2 && f == 1)
+            static_for<0, NB>([&](auto I) { Zh[(idx * NB + decltype(I)::value) * CC] = b[decltype(I)::value]; });
+    }
+    if (mode == 2) __syncthreads();
+    const bool inv = mode != 2 || f == 0;
+    if (idx < F::BT && inv) {
+        if (mode == 2)
+            static_for<0, NB>([&](auto I) {
+                b[decltype(I)::value] = cadd(b[decltype(I)::value], Zh[(idx * NB + decltype(I)::value) * CC]);
+            });
+        F::template inv_b_t<CC>(b, idx, Z1f, twM);
+    }
+    __syncthreads();
+    if (idx < F::MT && inv) F::template inv_m<CC>(idx, Z1f, Z2f, twA);
+    __syncthreads();
+    if (idx < F::AT && colok && inv) {
+        F::template inv_a_load<CC>(a, idx, Z2f);
+        F::inv_a(a);
+        float2* dst = f == 0 ? A : B;
+        static_for<0, NA>([&](auto I) {
+            constexpr int n1 = decltype(I)::value;
+            dst[base + size_t(idx + F::AT * n1) * g.hp] = a[n1];
+        });
+    }
+}
+
+template <int NA, int NM, int NB, int CC>
+__global__ void __launch_bounds__(2 * CC * Fft3<NA, NM, NB>::T) kf_col3(Geo g, float2* __restrict__ A,
+                                                                       float2* __restrict__ B, int mode, int op,
+                                                                       float scale) {
+    col3_body<NA, NM, NB, CC>(g, LaunchedCtx{int(blockIdx.x), int(blockIdx.y)}, A, B, mode, op, scale);
+}
+
 // Split the natural-order spectra W[j] (of a_j + i b_j) of nseq rows into half spectra:
 // a_j -> row rowa(j), b_j -> row rowb(j).
 template <class F, int ZR, class RowA, class RowB>
@@ -836,6 +932,26 @@ struct FixedImpl {
     }
     static FixedOps ops() {
         return FixedOps{F::N, RR, CC, &configure, &col, &row_u, &row_rho, &row_adj_rho, nullptr, nullptr, nullptr};
+    }
+};
+
+// Column passes on the three-level transform (only the column pass of the launch table;
+// combined with row passes of other impls through MixedImpl).
+template <int NA, int NM, int NB, int CC>
+struct Col3Impl {
+    using F = Fft3<NA, NM, NB>;
+    static constexpr int cc = CC;
+    static constexpr size_t smem_col = (F::N + F::N2 + 2 * F::N * CC + 4 * F::ZS * CC) * sizeof(float2);
+    static_assert(F::ZS >= F::N, "product hand-off fits one field's buffer");
+    static int configure() {
+        cudaError_t e = cudaFuncSetAttribute((const void*)kf_col3<NA, NM, NB, CC>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem_col));
+        return e == cudaSuccess ? PAT_OK : cuda_fail(e, "cudaFuncSetAttribute(kf_col3)");
+    }
+    static void col(const Geo& g, cudaStream_t st, float2* A, float2* B, int mode, int op, float scale) {
+        dim3 grid((g.hc + CC - 1) / CC, g.K);
+        launch_pdl(kf_col3<NA, NM, NB, CC>, grid, dim3(2 * CC * F::T), smem_col, st, true, g, A, B, mode, op,
+                   scale);
     }
 };
 

@@ -2,7 +2,9 @@
 // passes on the 20 x 15 factorisation, density passes on 15 x 20 (fewer registers where the
 // state is preloaded), and 8-column tiles for the column passes of the forward sweep, which
 // runs alone on the GPU; 1 all 20 x 15, 4 rows / 4 columns per CTA; 2 the same with 8 rows /
-// 2 columns; 3 state staged in shared memory by TMA bulk copies; 4 all 15 x 20; 5 as 0 with 8 rows per CTA in the row passes; 6 as 0 with the segment recompute's row passes staged by TMA (fewer registers beside the adjoint).
+// 2 columns; 3 state staged in shared memory by TMA bulk copies; 4 all 15 x 20; 5 as 0 with 8 rows per CTA in the row passes; 6 as 0 with the segment recompute's row passes staged by TMA (fewer registers beside the adjoint); 7 as 5 with the column
+// passes on the three-level 5 x 10 x 6 transform (60 threads per column: 4 columns per CTA,
+// 8 in the forward sweep); 8 the same with 2 and 4 columns per CTA.
 #include "kfixed.cuh"
 
 namespace pat {
@@ -17,13 +19,17 @@ using B8 = FixedImpl<15, 20, 8, 2, false>;   // density rows, 8 rows per CTA
 using SB = FixedImpl<15, 20, 4, 4, true>;    // density rows staged by TMA (segment recompute)
 using PA = FixedImpl<20, 15, 8, 4, false>;   // persistent sweep: columns and velocity rows
 using PB = FixedImpl<15, 20, 8, 4, false>;   // persistent sweep: density rows
+using T4 = Col3Impl<5, 10, 6, 4>;            // three-level column passes
+using T8 = Col3Impl<5, 10, 6, 8>;
+using T2 = Col3Impl<5, 10, 6, 2>;
 }  // namespace
 
 const FixedOps* fixed_ops_300(int v) {
     static const FixedOps ops[] = {MixedImpl<A4, A4, B4, B4, C8>::ops(), A4::ops(), A8::ops(), S4::ops(), B4::ops(),
                                    MixedImpl<A4, A8, B8, B8, C8>::ops(),
-                                   MixedImpl<A4, A4, B4, B4, C8, S4, SB>::ops()};
-    return (v >= 0 && v < 7) ? &ops[v] : nullptr;
+                                   MixedImpl<A4, A4, B4, B4, C8, S4, SB>::ops(),
+                                   MixedImpl<T4, A8, B8, B8, T8>::ops(), MixedImpl<T2, A8, B8, B8, T4>::ops()};
+    return (v >= 0 && v < int(sizeof(ops) / sizeof(ops[0]))) ? &ops[v] : nullptr;
 }
 
 const SweepOps* sweep_ops_300() {

@@ -1,14 +1,15 @@
 // Host-side check of the register FFT building blocks used by the fixed-size
-// row and column passes (two-level Cooley-Tukey transform of fft2l.cuh).
+// row and column passes (two- and three-level Cooley-Tukey transforms of fft2l.cuh).
 // Every function exercised here is __host__ __device__, so the same code that
 // runs in the kernels runs on the CPU; no CUDA call is made.
 //
 // Input (binary, little-endian) on stdin: int32 count, then per case
-// int32 N1, int32 N2, float32 x[2 N] (interleaved re, im).
+// int32 N1, int32 N2, int32 N3, float32 x[2 N] (interleaved re, im); N3 = 0 selects the
+// two-level transform N = N1 N2, otherwise the three-level N = N1 N2 N3 (A, M, B steps).
 // Output on stdout, per case: float32 X[2 N] (forward DFT through the A and B
 // layouts), float32 y[2 N] (inverse of X through the B and A layouts, not
 // normalised), float32 d[2 N1], float32 e[2 N2] (forward register DFTs of the
-// first N1 and N2 samples).
+// first N1 and N2 samples; three-level: of the first NA and NB samples).
 #include <cmath>
 #include <cstdio>
 #include <cstdint>
@@ -102,6 +103,67 @@ void run_case(const std::vector<float2>& x) {
     write_all(e, sizeof(e));
 }
 
+
+// three-level: A step (thread n2), M step (thread k1 NB + n_b), B step (thread kk)
+template <int NA, int NM, int NB>
+void run_case3(const std::vector<float2>& x) {
+    using F = Fft3<NA, NM, NB>;
+    constexpr int N = F::N, N2 = F::N2;
+    std::vector<float2> tw(N);
+    for (int q = 0; q < N; ++q) {
+        const double a = -2.0 * 3.14159265358979323846 * double(q) / double(N);
+        tw[q] = make_float2(float(std::cos(a)), float(std::sin(a)));
+    }
+    std::vector<float2> twA(N), twM(N2), Z0(F::ZS), Z1(F::ZS), X(N), y(N);
+    F::fill_tables(twA.data(), twM.data(), tw.data(), 0, 1);
+    for (int n2 = 0; n2 < N2; ++n2) {
+        float2 a[NA];
+        for (int n1 = 0; n1 < NA; ++n1) a[n1] = x[N2 * n1 + n2];
+        F::fwd_a_t(a, n2, Z0.data(), twA.data());
+    }
+    for (int t = 0; t < F::MT; ++t) F::fwd_m(t, Z0.data(), Z1.data(), twM.data());
+    for (int kk = 0; kk < F::BT; ++kk) {
+        float2 b[NB];
+        F::fwd_b_load(b, kk, Z1.data());
+        F::fwd_b(b);
+        for (int kb = 0; kb < NB; ++kb) X[kk + F::BT * kb] = b[kb];
+    }
+    for (int kk = 0; kk < F::BT; ++kk) {
+        float2 b[NB];
+        for (int kb = 0; kb < NB; ++kb) b[kb] = X[kk + F::BT * kb];
+        F::inv_b_t(b, kk, Z0.data(), twM.data());
+    }
+    for (int t = 0; t < F::MT; ++t) F::inv_m(t, Z0.data(), Z1.data(), twA.data());
+    for (int n2 = 0; n2 < N2; ++n2) {
+        float2 a[NA];
+        F::inv_a_load(a, n2, Z1.data());
+        F::inv_a(a);
+        for (int n1 = 0; n1 < NA; ++n1) y[n2 + N2 * n1] = a[n1];
+    }
+    float2 d[NA], e[NB];
+    for (int i = 0; i < NA; ++i) d[i] = x[i];
+    for (int i = 0; i < NB; ++i) e[i] = x[i];
+    dft<NA, false>(d);
+    dft<NB, false>(e);
+    write_all(X.data(), N * sizeof(float2));
+    write_all(y.data(), N * sizeof(float2));
+    write_all(d, sizeof(d));
+    write_all(e, sizeof(e));
+}
+
+template <int NA, int NM, int NB>
+bool dispatch_three(int a, int m, int b, const std::vector<float2>& x) {
+    if (a != NA || m != NM || b != NB) return false;
+    run_case3<NA, NM, NB>(x);
+    return true;
+}
+
+bool dispatch3(int a, int m, int b, const std::vector<float2>& x) {
+    return dispatch_three<5, 10, 6>(a, m, b, x) || dispatch_three<5, 12, 5>(a, m, b, x) ||
+           dispatch_three<5, 6, 10>(a, m, b, x) || dispatch_three<4, 3, 9>(a, m, b, x) ||
+           dispatch_three<3, 4, 5>(a, m, b, x) || dispatch_three<2, 3, 2>(a, m, b, x);
+}
+
 // the factorisations of the compiled grid sides (both orders)
 template <int N1, int N2>
 bool dispatch_one(int n1, int n2, const std::vector<float2>& x) {
@@ -125,12 +187,13 @@ int main() {
     int32_t count = 0;
     if (!read_all(&count, sizeof(count))) return 2;
     for (int c = 0; c < count; ++c) {
-        int32_t nn[2];
+        int32_t nn[3];
         if (!read_all(nn, sizeof(nn))) return 2;
-        std::vector<float2> x(size_t(nn[0]) * nn[1]);
+        std::vector<float2> x(size_t(nn[0]) * nn[1] * (nn[2] ? nn[2] : 1));
         if (!read_all(x.data(), x.size() * sizeof(float2))) return 2;
-        if (!dispatch(nn[0], nn[1], x)) {
-            std::fprintf(stderr, "no factorisation %d x %d compiled in\n", nn[0], nn[1]);
+        const bool ok = nn[2] ? dispatch3(nn[0], nn[1], nn[2], x) : dispatch(nn[0], nn[1], x);
+        if (!ok) {
+            std::fprintf(stderr, "no factorisation %d x %d x %d compiled in\n", nn[0], nn[1], nn[2]);
             return 3;
         }
     }
