@@ -150,6 +150,26 @@ int pat_plan_variant(pat_plan plan);
 int pat_plan_set_persistent(pat_plan plan, int enable);
 int pat_plan_persistent(pat_plan plan);
 
+/* Cluster-resident stepping (Sec. 2.1 scheme; grid side 300): with enable != 0
+ * every forward sweep of the plan and every segment recompute of the reverse
+ * sweep runs as one launch of one thread-block cluster of 16 CTAs per data
+ * set, which keeps the data set's wavefield in registers and shared memory
+ * for all its time steps and exchanges row and column spectra through
+ * distributed shared memory (four cluster barriers per step).  Same scheme
+ * and results as the launched passes to FP32 rounding; traces, checkpoints,
+ * pressure history and the final state are written as by the launched
+ * sweep.  Clusters that do not fit on the GPU at once run after the others.
+ * PAT_EINVAL for other grid sides; PAT_ECUDA if the GPU cannot run a
+ * 16-CTA cluster of this size.  pat_plan_cluster returns 1 if enabled, 0 if
+ * not, -1 for a NULL plan; pat_plan_cluster_capacity the number of such
+ * clusters (data sets) the current GPU runs at once (0 if none or no
+ * cluster-resident stepping for the plan's grid side; PAT_EINVAL for a NULL
+ * plan).  The launched passes are faster on GB300 at every K measured (the
+ * cluster form is an option, off by default). */
+int pat_plan_set_cluster(pat_plan plan, int enable);
+int pat_plan_cluster(pat_plan plan);
+int pat_plan_cluster_capacity(pat_plan plan);
+
 /* CUDA graphs: with enable != 0, the first pat_forward / pat_adjoint_grad
  * (or objective evaluation of pat_reconstruct) on a non-default stream with
  * a given set of buffers and kernel variant is captured into a CUDA graph and

@@ -95,6 +95,9 @@ SIGNATURES = {
     "pat_selftest_queue": (c_int, [c_void_p, c_void_p, ctypes.c_uint, c_void_p]),
     "pat_plan_set_persistent": (c_int, [c_void_p, c_int]),
     "pat_plan_persistent": (c_int, [c_void_p]),
+    "pat_plan_set_cluster": (c_int, [c_void_p, c_int]),
+    "pat_plan_cluster": (c_int, [c_void_p]),
+    "pat_plan_cluster_capacity": (c_int, [c_void_p]),
     "pat_prior_create": (c_int, [c_int, c_double, c_double, c_int, POINTER(c_void_p)]),
     "pat_prior_destroy": (c_int, [c_void_p]),
     "pat_prior_xi": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_void_p]),

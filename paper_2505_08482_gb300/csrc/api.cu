@@ -66,6 +66,9 @@ int pat::forward_sweep(pat_plan_s* p, const float* c, const float* p0, float* y,
     float* hlast = keep ? hist_of(p, w, p->nseg - 1) : nullptr;
     if (p->persistent && p->sweep)   // one launch: initial pass, every step, checkpoints, history
         return launch_forward_persistent(L, w, p0, y, hlast, last0, keep ? w.ckpt : nullptr);
+    if (p->cluster && p->clops)      // one cluster per data set for the whole sweep, state on chip
+        return launch_forward_cluster(L, w, p0, nullptr, 0, p->nt - 1, y, hlast, last0, keep ? w.ckpt : nullptr,
+                                      w.ux);
     RC(launch_row_rho(L, w, 1, p0, y, 0, (keep && last0 == 0) ? hlast : nullptr, 0));
     // segments of s steps with the state copied at their starts (one segment without checkpoints)
     const int seg = keep ? p->s_eff : p->nt;
@@ -95,6 +98,9 @@ int recompute(pat_plan_s* p, const float* p0, const Ws& w, int j, cudaStream_t s
     const int n0 = j * p->s_eff;
     const int n1 = std::min(n0 + p->s_eff, p->nt) - 1;
     float* h = hist_of(p, w, j);
+    if (p->cluster && p->clops)   // from the checkpoint (or p0) on chip, storing p^n of the segment
+        return launch_forward_cluster(L, w, p0, j == 0 ? nullptr : w.ckpt + size_t(j - 1) * 4 * f, n0, n1, nullptr,
+                                      h, n0, nullptr, nullptr);
     if (j == 0) {
         RC(launch_row_rho(L, w, 1, p0, nullptr, 0, h, 0));
     } else {
@@ -172,7 +178,7 @@ template <class F>
 int with_graph(pat_plan_s* p, int kind, const std::array<const void*, 10>& key, size_t ws_bytes, cudaStream_t st,
                F&& body) {
     if (!p->use_graphs || st == nullptr) return body();
-    const int gv = 2 * p->variant + (p->persistent ? 1 : 0);   // kernel variant and sweep form
+    const int gv = 4 * p->variant + (p->persistent ? 1 : 0) + (p->cluster ? 2 : 0);   // variant and sweep form
     for (auto& g : p->graphs)
         if (g.kind == kind && g.variant == gv && g.key == key && g.ws_bytes == ws_bytes) {
             PAT_CUDA(cudaGraphLaunch(g.exec, st));

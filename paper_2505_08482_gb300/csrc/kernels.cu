@@ -21,6 +21,7 @@
 #include "pat_internal.h"
 #include "geo.cuh"
 #include "kfixed.cuh"
+#include "kcluster.cuh"
 
 namespace pat {
 
@@ -619,6 +620,35 @@ int launch_row_rho(const Launch& L, const Ws& w, int mode, const float* p0, floa
                                                            tstep, hist, hist_slot, p->R);
     prof_end(PAT_K_ROW_RHO, L.st);
     return check_launch("k_row_rho");
+}
+
+int launch_forward_cluster(const Launch& L, const Ws& w, const float* p0, const float* state, int n0, int n1,
+                           float* y, float* hist, int hist_base, float* ckpt, float* state_out) {
+    const pat_plan_s* p = L.p;
+    if (!p->clops) {
+        set_error("no cluster-resident stepping for grid side %d", p->ng);
+        return PAT_EINVAL;
+    }
+    const double nrm = double(p->ng) * p->ng;
+    ClusterArgs a;
+    a.cg = w.cg;
+    a.p0 = p0;
+    a.state = state;
+    a.state_out = state_out;
+    a.y = y;
+    a.hist = hist;
+    a.hist_base = hist_base;
+    a.ckpt = ckpt;
+    a.s = p->s_eff;
+    a.n0 = n0;
+    a.n1 = n1;
+    a.init = state ? 0 : 1;
+    a.sg = float(p->g.dt / p->g.rho0 / nrm);
+    a.sd = float(p->g.dt * p->g.rho0 / nrm);
+    count_launch();
+    int rc = p->clops->forward(geo_ws(p, w), L.st, a);
+    if (rc != PAT_OK) return rc;
+    return check_launch("kc_forward");
 }
 
 int launch_forward_persistent(const Launch& L, const Ws& w, const float* p0, float* y, float* hist, int last0,

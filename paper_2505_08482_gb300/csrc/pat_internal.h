@@ -16,6 +16,7 @@ namespace pat {
 
 struct FixedOps;
 struct SweepOps;
+struct ClusterOps;
 void set_error(const char* fmt, ...);
 int cuda_fail(cudaError_t e, const char* where);
 
@@ -70,6 +71,8 @@ struct pat_plan_s {
     const pat::FixedOps* fast;   // fixed-size passes for this grid side (nullptr: generic Stockham)
     const pat::SweepOps* sweep;  // persistent forward sweep of this grid side (nullptr: none)
     bool persistent;             // forward sweeps run as one persistent launch
+    const pat::ClusterOps* clops;   // cluster-resident stepping of this grid side (nullptr: none)
+    bool cluster;                // forward sweeps and segment recomputes run cluster-resident
     int variant;       // -1 generic, else index of the fixed-size tile variant
     int R;             // rows per CTA in row passes (even)
     int C;             // spectral columns per CTA in column passes
@@ -155,6 +158,13 @@ int launch_row_adj_final2(const Launch& L, const Ws& w, const float* p0, float* 
 int launch_reduce_cbar(const Launch& L, const Ws& w, float* grad_c);
 int launch_residual(const Launch& L, const Ws& w, const float* ypred, const float* ymeas,
                     const float* wts, float* resid, double* J_out);
+
+// cluster-resident forward steps n0 .. n1-1 (kcluster.cuh): from p0 (init, n0 = 0) or from the
+// state [4][K][ng][ng] at level n0; traces into y (or null), pressure history of levels
+// >= hist_base into hist (or null), checkpoints every s levels into ckpt (or null), the final
+// state into state_out (or null)
+int launch_forward_cluster(const Launch& L, const Ws& w, const float* p0, const float* state, int n0, int n1,
+                           float* y, float* hist, int hist_base, float* ckpt, float* state_out);
 
 // ---- api.cu internals ----
 // Forward sweep into y [K][nt][m] with workspace regions w (checkpoints kept if keep).

@@ -10,6 +10,7 @@
 
 #include "pat_internal.h"
 #include "kfixed.cuh"
+#include "kcluster.cuh"
 
 namespace pat {
 
@@ -182,6 +183,33 @@ extern "C" int pat_plan_set_persistent(pat_plan plan, int enable) {
 
 extern "C" int pat_plan_persistent(pat_plan plan) { return plan ? int(plan->persistent) : -1; }
 
+extern "C" int pat_plan_set_cluster(pat_plan plan, int enable) {
+    if (!plan) { set_error("pat_plan_set_cluster: null plan"); return PAT_EINVAL; }
+    if (!enable) {
+        plan->cluster = false;
+        return PAT_OK;
+    }
+    const ClusterOps* co = cluster_ops_for(plan->ng);
+    if (!co) {
+        set_error("pat_plan_set_cluster: grid side %d has no cluster-resident stepping (side 300)", plan->ng);
+        return PAT_EINVAL;
+    }
+    int rc = co->configure();
+    if (rc != PAT_OK) return rc;
+    plan->clops = co;
+    plan->cluster = true;
+    return PAT_OK;
+}
+
+extern "C" int pat_plan_cluster(pat_plan plan) { return plan ? int(plan->cluster) : -1; }
+
+extern "C" int pat_plan_cluster_capacity(pat_plan plan) {
+    if (!plan) { set_error("pat_plan_cluster_capacity: null plan"); return PAT_EINVAL; }
+    const ClusterOps* co = plan->clops ? plan->clops : cluster_ops_for(plan->ng);
+    if (!co || co->configure() != PAT_OK) return 0;
+    return co->capacity();
+}
+
 extern "C" int pat_plan_set_graphs(pat_plan plan, int enable) {
     if (!plan) { set_error("pat_plan_set_graphs: null plan"); return PAT_EINVAL; }
     plan->use_graphs = enable != 0;
@@ -240,6 +268,8 @@ extern "C" int pat_plan_create_batched(pat_plan* out, const pat_grid* g, int m, 
     p->hist_valid_ws = nullptr;
     p->sweep = nullptr;
     p->persistent = false;
+    p->clops = nullptr;
+    p->cluster = false;
     p->use_graphs = false;
     p->graph_clock = 0;
     p->side = nullptr;

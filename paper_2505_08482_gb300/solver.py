@@ -199,6 +199,22 @@ class Plan:
         with torch.cuda.device(self.device):
             B.check(B.lib().pat_plan_set_persistent(self._h, int(bool(enable))), "pat_plan_set_persistent")
 
+    @property
+    def cluster(self) -> bool:
+        """Forward sweeps and segment recomputes cluster-resident (pat_plan_set_cluster)."""
+        return bool(B.lib().pat_plan_cluster(self._h) == 1)
+
+    @cluster.setter
+    def cluster(self, enable: bool):
+        with torch.cuda.device(self.device):
+            B.check(B.lib().pat_plan_set_cluster(self._h, int(bool(enable))), "pat_plan_set_cluster")
+
+    @property
+    def cluster_capacity(self) -> int:
+        """Clusters (data sets) of the cluster-resident form the GPU runs at once (0: unavailable)."""
+        with torch.cuda.device(self.device):
+            return int(B.lib().pat_plan_cluster_capacity(self._h))
+
     def set_graphs(self, enable: bool = True):
         """Capture whole calls into CUDA graphs and replay them (pat_plan_set_graphs)."""
         B.check(B.lib().pat_plan_set_graphs(self._h, int(bool(enable))), "pat_plan_set_graphs")

@@ -43,9 +43,12 @@ def test_null_plans_and_buffers(L, B):
                  lambda: L.pat_vjp(None, FAKE, FAKE, FAKE, FAKE, FAKE, FAKE, 1 << 20, None),
                  lambda: L.pat_plan_autotune(None, None, 0, None, None),
                  lambda: L.pat_plan_set_graphs(None, 1),
+                 lambda: L.pat_plan_set_cluster(None, 1),
+                 lambda: L.pat_plan_cluster_capacity(None),
                  lambda: L.pat_status(None, FAKE, ctypes.byref(ctypes.c_int()), None)):
         assert call() == B.PAT_EINVAL
         assert L.pat_last_error()
+    assert L.pat_plan_cluster(None) == -1
 
 
 def test_noalloc_null_arguments(L, B):
