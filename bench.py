@@ -89,6 +89,11 @@ def parse():
     ap.add_argument("--no-graphs", action="store_true", help="launch every kernel from the host (no CUDA graphs)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-ttr", action="store_true", help="skip the time-to-relative-error comparison")
+    ap.add_argument("--no-ws-sample", action="store_true",
+                    help="skip the reduced warm-start comparison of the default line")
+    ap.add_argument("--ws-sample-train", type=int, default=2048, help="training pairs of the reduced warm start")
+    ap.add_argument("--ws-sample-test", type=int, default=64, help="held-out seeds of the reduced warm start")
+    ap.add_argument("--ws-sample-epochs", type=int, default=6)
     ap.add_argument("--ttr-instances", type=int, default=8)
     ap.add_argument("--ttr-ec", type=float, default=2.0, help="E_c target (%%) of the time-to-target comparison")
     ap.add_argument("--ttr-ep0", type=float, default=50.0, help="E_p0 target (%%) of the time-to-target comparison")
@@ -634,6 +639,8 @@ def run_ours(args, rank, world, local_rank):
                                 "plain64_unscaled_s": oracle_plain64()}
     if rank == 0 and world == 1 and not args.no_ttr:
         line["time_to_rel_err"] = time_to_rel_err(args, dev)
+        if not args.no_ws_sample:
+            line["time_to_rel_err"]["warm_start"] = warm_start_sample(args)
     if rank == 0:
         print(json.dumps(line), flush=True)
 
@@ -704,8 +711,73 @@ def time_to_rel_err(args, dev):
             "batched": {"wall_s": wall_b, "latency_s_p50": wall_b, "latency_s_p99": wall_b,
                         "reached": sum(ok_b) / len(ok_b),
                         "iterations_median": float(np.median([len(r[2]) for r in res]))},
-            "speedup_batched_vs_plain": wall_plain / wall_b,
-            "warm_start": "bench.py --warmstart (trains the U-Net first: minutes)"}
+            "speedup_batched_vs_plain": wall_plain / wall_b}
+
+
+def warm_start_sample(args):
+    """The learned warm start against the plain start on a reduced sample of its workload:
+    the U-Net (4 levels x 32 channels, BF16 on the tcgen05 tensor cores) trained on
+    ws_sample_train solver-generated pairs (128 x 128, K = 4, M = 256, Nt = 600, 2-8 inclusions)
+    for ws_sample_epochs epochs, then ws_sample_test held-out seeds reconstructed from each start
+    (levels 64 -> 128, at most ttr_iters L-BFGS iterations per level, every instance in one batched
+    call per arm, each instance stopping once E_c <= ttr_ec and E_p0 <= ttr_ep0, Eq. RelativeError).
+    The full-size run (20,000 pairs, 512 seeds) is bench.py --warmstart.
+    """
+    import numpy as np
+    import torch
+
+    from paper_2505_08482_gb300.solver import ReconConfig, reconstruct_batched
+    from paper_2505_08482_gb300.warmstart import (PairGenerator, UNet, init_params, iterations_to, predict_c,
+                                                  relative_error, train)
+    n, K = 128, 4
+    gen = PairGenerator(n=n, K=K, M=256, nt=600, batch=64)
+    t0 = time.perf_counter()
+    X, T, _ = gen.make(list(range(args.ws_sample_train)))
+    torch.cuda.synchronize()
+    t_gen = time.perf_counter() - t0
+    net = UNet(4, 32, K, n, n, max_batch=32)
+    net.set_params(init_params(4, 32, K, seed=1))
+    t0 = time.perf_counter()
+    hist = train(net, X, T, epochs=args.ws_sample_epochs, batch=32, lr=1e-3)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    del X, T
+    Xh, _, raw = gen.make(list(range(10 ** 6, 10 ** 6 + args.ws_sample_test)), keep_data=True)
+    c_true = torch.stack([r["c_true"] for r in raw])
+    t0 = time.perf_counter()
+    c_warm = predict_c(net, Xh)
+    torch.cuda.synchronize()
+    t_pred = time.perf_counter() - t0
+    c_plain = torch.stack([torch.full_like(ct, 0.5 * float(ct.min() + ct.max())) for ct in c_true])
+    cfg = ReconConfig(levels=(64, n), L=n * 1e-4, dt_data=gen.gs.dt, nt_data=gen.nt, sensors_xy=gen.sensors, K=K,
+                      iters=args.ttr_iters, mem=20, ckpt_every=32, rtol=0.0)
+    out = {}
+    for name, cinit in (("plain", c_plain), ("warm", c_warm)):
+        insts = [dict(y_meas=r["y_meas"].contiguous(), w=r["w"].contiguous(), c_init=cinit[j].contiguous(),
+                      c_true=r["c_true"].contiguous(), p0_true=r["p0_true"].contiguous(), ec_target=args.ttr_ec,
+                      ep0_target=args.ttr_ep0) for j, r in enumerate(raw)]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        res, _ = reconstruct_batched(cfg, insts)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        its = [iterations_to(rows, args.ttr_ec, 2, args.ttr_ep0) for _, _, rows, _ in res]
+        reached = [i for i, _ in its if i is not None]
+        out[name] = {"initial_Ec_median": float(np.median(relative_error(cinit, c_true).cpu().numpy())),
+                     "reached": len(reached) / len(its),
+                     "iterations_median": float(np.median(reached)) if reached else None,
+                     "ms_median": float(np.median([m for i, m in its if i is not None])) if reached else None,
+                     "wall_s_batched": wall}
+    out["warm"]["prediction_s"] = t_pred
+    return {"workload": f"reduced sample of the warm-start workload: U-Net 4 levels x 32 trained on "
+                        f"{args.ws_sample_train} solver-generated pairs (128x128, K=4, M=256, Nt=600, 2-8 "
+                        f"inclusions) for {args.ws_sample_epochs} epochs, {args.ws_sample_test} held-out seeds, "
+                        f"levels 64->128; the full run is bench.py --warmstart",
+            "targets": {"E_c_pct": args.ttr_ec, "E_p0_pct": args.ttr_ep0, "max_iterations_per_level": args.ttr_iters},
+            "pair_generation_s": t_gen, "training_s": t_train, "train_loss_first_last": [hist[0], hist[-1]],
+            "plain": out["plain"], "warm": out["warm"],
+            "speedup_warm_vs_plain_median_ms": (out["plain"]["ms_median"] / out["warm"]["ms_median"])
+            if out["plain"]["ms_median"] and out["warm"]["ms_median"] else None}
 
 
 def run_batch(args):
