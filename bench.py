@@ -106,6 +106,8 @@ def parse():
     ap.add_argument("--batch-instances", type=int, default=64)
     ap.add_argument("--batch-iters", type=int, default=2)
     ap.add_argument("--batch-plain", type=int, default=64, help="instances also solved one by one")
+    ap.add_argument("--batch-sample", type=int, default=16,
+                    help="instances of the reduced batched sweep in the default line (0: none)")
     ap.add_argument("--persistent", action="store_true",
                     help="--batch: forward sweeps of the batched arm as persistent launches")
     ap.add_argument("--roofline-k", type=int, default=0,
@@ -641,6 +643,11 @@ def run_ours(args, rank, world, local_rank):
         line["time_to_rel_err"] = time_to_rel_err(args, dev)
         if not args.no_ws_sample:
             line["time_to_rel_err"]["warm_start"] = warm_start_sample(args)
+        if args.batch_sample > 0:
+            # the batched serving-style sweep on a reduced sample (all of it also solved one by one)
+            b = batch_sweep(args.batch_sample, args.batch_sample, args.batch_iters, False)
+            b["config"]["workload"] = "reduced sample (bench.py --batch runs 64): " + b["config"]["workload"]
+            line["batched_sweep"] = b
     if rank == 0:
         print(json.dumps(line), flush=True)
 
@@ -782,6 +789,15 @@ def warm_start_sample(args):
 
 def run_batch(args):
     """Batched serving-style sweep (two-level multigrid N/2 -> N per instance)."""
+    print(json.dumps(batch_sweep(args.batch_instances, args.batch_plain, args.batch_iters, args.persistent)),
+          flush=True)
+
+
+def batch_sweep(n_inst, n_plain, iters, persistent):
+    """n_inst reconstructions with N ~ U{96,128,160,192,256}, K ~ U{1,2,4,8}, M = 2N, Nt = 7N (two
+    multigrid levels N/2 -> N, iters L-BFGS iterations per level), solved batched (one
+    pat_reconstruct_batched call per grid side, the sides concurrently) and about n_plain of them
+    one by one; returns the measurement line."""
     import threading
 
     import numpy as np
@@ -796,7 +812,7 @@ def run_batch(args):
     dev = torch.device("cuda", 0)
     rng = ps.rng_for(2024)
     sides = [96, 128, 160, 192, 256]
-    specs = [(int(rng.choice(sides)), int(rng.choice([1, 2, 4, 8]))) for _ in range(args.batch_instances)]
+    specs = [(int(rng.choice(sides)), int(rng.choice([1, 2, 4, 8]))) for _ in range(n_inst)]
     dx, c_hi = 1e-4, 1750.0
     f32 = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float32, device=dev)
     groups = {}
@@ -825,8 +841,8 @@ def run_batch(args):
                            c_init=f32(np.full((n, n), 0.5 * (c.min() + c.max()))))
             k0 += K
         data[("cfg", n)] = ReconConfig(levels=(n // 2, n), L=n * dx, dt_data=gs.dt, nt_data=nt, sensors_xy=xy, K=1,
-                                       iters=args.batch_iters, mem=20, ckpt_every=32, autotune=True,
-                                       persistent=args.persistent)
+                                       iters=iters, mem=20, ckpt_every=32, autotune=True,
+                                       persistent=persistent)
     torch.cuda.synchronize()
     # batched: one call per grid side, the sides concurrently on their own streams
     lat = {}
@@ -867,7 +883,7 @@ def run_batch(args):
     plain, plain_arrival = {}, {}
     tp0 = time.perf_counter()
     for n, members in groups.items():
-        for i, K in members[: max(1, args.batch_plain * len(members) // len(specs))]:
+        for i, K in members[: max(1, n_plain * len(members) // len(specs))]:
             cfg = data[("cfg", n)]
             cfg.K = K
             cfg.autotune = False
@@ -885,7 +901,7 @@ def run_batch(args):
     line = {"metric": "batched sweep aggregate Gcell-steps/s", "value": cell_steps / wall / 1e9,
             "unit": "Gcell-steps/s", "n_gpus": 1, "higher_is_better": True, "dtype": "f32", "data": "synthetic",
             "config": {"workload": f"{len(specs)} reconstructions, N~U{{96..256}}, K~U{{1,2,4,8}}, M=2N, Nt=7N, "
-                                   f"levels N/2->N, {args.batch_iters} L-BFGS iterations per level",
+                                   f"levels N/2->N, {iters} L-BFGS iterations per level",
                        "groups": {str(n): len(m) for n, m in groups.items()}},
             "wall_s": wall, "latency_ms_p50": q(lats, 50), "latency_ms_p99": q(lats, 99),
             "plain_wall_s_scaled": plain_wall / frac if frac > 0 else None,
@@ -896,10 +912,10 @@ def run_batch(args):
                             "is done when they are served one after another",
             "plain_arrival_latency_ms_p50": q(sorted(plain_arrival.values()), 50),
             "plain_arrival_latency_ms_p99": q(sorted(plain_arrival.values()), 99),
-            "persistent_sweeps": bool(args.persistent),
+            "persistent_sweeps": bool(persistent),
             "plain_instances_timed": len(plain), "gpu_launches": batched_launches,
             "speedup_vs_plain": (plain_wall / frac) / wall if frac > 0 else None}
-    print(json.dumps(line), flush=True)
+    return line
 
 
 def run_roofline_k(args):
