@@ -4,7 +4,8 @@
 // runs alone on the GPU; 1 all 20 x 15, 4 rows / 4 columns per CTA; 2 the same with 8 rows /
 // 2 columns; 3 state staged in shared memory by TMA bulk copies; 4 all 15 x 20; 5 as 0 with 8 rows per CTA in the row passes; 6 as 0 with the segment recompute's row passes staged by TMA (fewer registers beside the adjoint); 7 as 5 with the column
 // passes on the three-level 5 x 10 x 6 transform (60 threads per column: 4 columns per CTA,
-// 8 in the forward sweep); 8 the same with 2 and 4 columns per CTA.
+// 8 in the forward sweep); 8 the same with 2 and 4 columns per CTA; 9 as 5 with 4-column tiles
+// for the column passes of the forward sweep too (more CTAs per SM when a launch has many waves).
 #include "kfixed.cuh"
 
 namespace pat {
@@ -28,7 +29,8 @@ const FixedOps* fixed_ops_300(int v) {
     static const FixedOps ops[] = {MixedImpl<A4, A4, B4, B4, C8>::ops(), A4::ops(), A8::ops(), S4::ops(), B4::ops(),
                                    MixedImpl<A4, A8, B8, B8, C8>::ops(),
                                    MixedImpl<A4, A4, B4, B4, C8, S4, SB>::ops(),
-                                   MixedImpl<T4, A8, B8, B8, T8>::ops(), MixedImpl<T2, A8, B8, B8, T4>::ops()};
+                                   MixedImpl<T4, A8, B8, B8, T8>::ops(), MixedImpl<T2, A8, B8, B8, T4>::ops(),
+                                   MixedImpl<A4, A8, B8, B8, A4>::ops()};
     return (v >= 0 && v < int(sizeof(ops) / sizeof(ops[0]))) ? &ops[v] : nullptr;
 }
 
