@@ -128,7 +128,19 @@ __device__ __forceinline__ void col_mults(const Geo& g, int kx, int ky, int op, 
 // The two fields (or the two outputs) of a column are handled by separate threads (f = 0, 1);
 // in mode 0 they share the first transform stage.
 // Tables and twiddles are staged before the dependency wait, the columns read after it.
-template <int N1, int N2, int CC, class Ctx>
+// LEAN = false: the multipliers MX, MY of the CTA's columns are tabulated in shared memory before
+// the dependency wait (off the critical path of a chain of passes); LEAN = true: they are formed
+// where they are used from the factors and kappa (less shared memory and fewer instructions, so
+// more CTAs per SM and a higher rate when a launch has many waves, at the cost of a longer
+// critical path after the wait).
+template <int N1, int N2, int CC, bool LEAN = false>
+struct ColSmem {
+    using F = Fft2<N1, N2>;
+    static constexpr int tables = LEAN ? 2 * F::N + CC + (F::N * CC + 1) / 2 : F::N + 2 * F::N * CC;   // float2
+    static constexpr size_t bytes = (size_t(tables) + 4 * F::ZS * CC) * sizeof(float2);
+};
+
+template <int N1, int N2, int CC, class Ctx, bool LEAN = false>
 __device__ __forceinline__ void col_body(const Geo& g, const Ctx& ctx, float2* __restrict__ A,
                                          float2* __restrict__ B, int mode, int op, float scale) {
     using F = Fft2<N1, N2>;
@@ -137,9 +149,14 @@ __device__ __forceinline__ void col_body(const Geo& g, const Ctx& ctx, float2* _
     constexpr int NT = 2 * CC * F::T;
     extern __shared__ float2 sm[];
     float2* tw = sm;                        // [N]
-    float2* MX = tw + N;                    // [N][CC] x multiplier at (ky, c)
-    float2* MY = MX + N * CC;               // [N][CC]
-    float2* Zf = MY + N * CC;               // forward transposes of the two threads' fields, [2][ZS][CC]
+    // LEAN: y factor of the pass's operator [N], x factors of the CTA's columns [CC], scale * kappa
+    // at (ky, c) [N][CC] (floats); else MX, MY at (ky, c) [N][CC] each
+    float2* FY = tw + N;
+    float2* FXC = FY + N;
+    float* KP = reinterpret_cast<float*>(FXC + CC);
+    float2* MX = tw + N;
+    float2* MY = MX + N * CC;
+    float2* Zf = sm + ColSmem<N1, N2, CC, LEAN>::tables;   // forward transposes of the two threads' fields, [2][ZS][CC]
     float2* Zi = Zf + 2 * F::ZS * CC;       // inverse transposes of the two outputs, [2][ZS][CC]
     const int k = ctx.k;
     const int f = threadIdx.x / (CC * F::T);
@@ -149,21 +166,48 @@ __device__ __forceinline__ void col_body(const Geo& g, const Ctx& ctx, float2* _
     const bool colok = kx < g.hc;
     const int kxc = colok ? kx : g.hc - 1;
     const size_t base = size_t(k) * N * g.hp + kxc;
-    static_for<0, (N + NT - 1) / NT>([&](auto I) {
-        const int i = decltype(I)::value * NT + threadIdx.x;
-        if (i < N) tw[i] = g.tw[i];
-    });
-    static_for<0, (N * CC + NT - 1) / NT>([&](auto I) {
-        const int i = decltype(I)::value * NT + threadIdx.x;
-        if (i < N * CC) {
-            const int cc = i % CC, ky = i / CC;
-            const int kxs = min(ctx.bx * CC + cc, g.hc - 1);
-            float2 mx, my;
-            col_mults(g, kxs, ky, op, scale, mx, my);
-            MX[i] = mx;
-            MY[i] = my;
+    if constexpr (LEAN) {
+        // MX = fx(kx) kap, MY = fy(ky) kap (kap = scale kappa(kx, ky); D: -conj of the G factors)
+        // are formed where they are used, from the factors and kappa staged here
+        static_for<0, (N + NT - 1) / NT>([&](auto I) {
+            const int i = decltype(I)::value * NT + threadIdx.x;
+            if (i < N) {
+                tw[i] = g.tw[i];
+                float2 v = g.fy[i];
+                if (op == 1) v.x = -v.x;
+                FY[i] = v;
+            }
+        });
+        if (threadIdx.x < CC) {
+            float2 v = g.fx[min(ctx.bx * CC + int(threadIdx.x), g.hc - 1)];
+            if (op == 1) v.x = -v.x;
+            FXC[threadIdx.x] = v;
         }
-    });
+        static_for<0, (N * CC + NT - 1) / NT>([&](auto I) {
+            const int i = decltype(I)::value * NT + threadIdx.x;
+            if (i < N * CC) {
+                const int cc = i / N, ky = i - cc * N;
+                const int kxs = min(ctx.bx * CC + cc, g.hc - 1);
+                KP[ky * CC + cc] = scale * g.kappa_t[size_t(kxs) * g.ng + ky];
+            }
+        });
+    } else {
+        static_for<0, (N + NT - 1) / NT>([&](auto I) {
+            const int i = decltype(I)::value * NT + threadIdx.x;
+            if (i < N) tw[i] = g.tw[i];
+        });
+        static_for<0, (N * CC + NT - 1) / NT>([&](auto I) {
+            const int i = decltype(I)::value * NT + threadIdx.x;
+            if (i < N * CC) {
+                const int cc = i % CC, ky = i / CC;
+                const int kxs = min(ctx.bx * CC + cc, g.hc - 1);
+                float2 mx, my;
+                col_mults(g, kxs, ky, op, scale, mx, my);
+                MX[i] = mx;
+                MY[i] = my;
+            }
+        });
+    }
     ctx.input_ready();
     float2* Zmine = Zf + f * F::ZS * CC + c;
     // mode 0 has one input: the f = 1 threads read the f = 0 threads' first transform stage
@@ -180,14 +224,23 @@ __device__ __forceinline__ void col_body(const Geo& g, const Ctx& ctx, float2* _
     if (idx < N2 && own_fwd) F::template fwd_a<CC>(a, idx, Zmine, tw);
     __syncthreads();
     float2 b[N2];
-    const float2* Mm = (f == 0) ? MX : MY;
     if (idx < N1) {
         F::template fwd_b_load<CC>(b, idx, own_fwd ? Zmine : Zf + c);
         F::fwd_b(b);
-        static_for<0, N2>([&](auto I) {
-            constexpr int k2 = decltype(I)::value;
-            b[k2] = cmul(b[k2], Mm[(idx + N1 * k2) * CC + c]);
-        });
+        if constexpr (LEAN) {
+            const float2 fxm = FXC[c];
+            static_for<0, N2>([&](auto I) {
+                constexpr int k2 = decltype(I)::value;
+                const int ky = idx + N1 * k2;
+                b[k2] = cmul(b[k2], cscale(f == 0 ? fxm : FY[ky], KP[ky * CC + c]));
+            });
+        } else {
+            const float2* Mm = (f == 0) ? MX : MY;
+            static_for<0, N2>([&](auto I) {
+                constexpr int k2 = decltype(I)::value;
+                b[k2] = cmul(b[k2], Mm[(idx + N1 * k2) * CC + c]);
+            });
+        }
         if (mode == 2 && f == 1) {   // hand the product to the f = 0 thread of the same column
             static_for<0, N2>([&](auto I) { Zi[((F::ZS + idx * N2 + decltype(I)::value) * CC) + c] = b[decltype(I)::value]; });
         }
@@ -217,6 +270,13 @@ __global__ void __launch_bounds__(2 * CC * Fft2<N1, N2>::T) kf_col(Geo g, float2
                                                                   float2* __restrict__ B, int mode, int op,
                                                                   float scale) {
     col_body<N1, N2, CC>(g, LaunchedCtx{int(blockIdx.x), int(blockIdx.y)}, A, B, mode, op, scale);
+}
+
+template <int N1, int N2, int CC>
+__global__ void __launch_bounds__(2 * CC * Fft2<N1, N2>::T) kf_col_lean(Geo g, float2* __restrict__ A,
+                                                                       float2* __restrict__ B, int mode, int op,
+                                                                       float scale) {
+    col_body<N1, N2, CC, LaunchedCtx, true>(g, LaunchedCtx{int(blockIdx.x), int(blockIdx.y)}, A, B, mode, op, scale);
 }
 
 // Column pass on the three-level transform (Fft3): the same modes and multipliers as col_body,
@@ -885,7 +945,7 @@ struct FixedImpl {
     using F = Fft2<N1, N2>;
     static constexpr int n1 = N1, n2 = N2, rr = RR, cc = CC;
     using RS = RowSmem<F, RR>;
-    static constexpr size_t smem_col = (F::N + 2 * F::N * CC + 4 * F::ZS * CC) * sizeof(float2);
+    static constexpr size_t smem_col = ColSmem<N1, N2, CC>::bytes;
     static_assert(2 * F::ZS >= F::ZS + F::N1 * F::N2, "product hand-off fits the inverse buffer");
     static_assert(!STAGE || (F::N % 4 == 0 && RR % 2 == 0), "staged row blocks are 16-byte multiples");
     // staged: velocity 2 arrays, density 3, adjoint density 4 and the dJ/dc rows (n < Ng)
@@ -951,6 +1011,25 @@ struct Col3Impl {
     static void col(const Geo& g, cudaStream_t st, float2* A, float2* B, int mode, int op, float scale) {
         dim3 grid((g.hc + CC - 1) / CC, g.K);
         launch_pdl(kf_col3<NA, NM, NB, CC>, grid, dim3(2 * CC * F::T), smem_col, st, true, g, A, B, mode, op,
+                   scale);
+    }
+};
+
+// Column passes with the multipliers formed where they are used (col_body LEAN; only the column
+// pass of the launch table, combined with row passes of other impls through MixedImpl).
+template <int N1, int N2, int CC>
+struct ColLeanImpl {
+    using F = Fft2<N1, N2>;
+    static constexpr int cc = CC;
+    static constexpr size_t smem_col = ColSmem<N1, N2, CC, true>::bytes;
+    static int configure() {
+        cudaError_t e = cudaFuncSetAttribute((const void*)kf_col_lean<N1, N2, CC>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem_col));
+        return e == cudaSuccess ? PAT_OK : cuda_fail(e, "cudaFuncSetAttribute(kf_col_lean)");
+    }
+    static void col(const Geo& g, cudaStream_t st, float2* A, float2* B, int mode, int op, float scale) {
+        dim3 grid((g.hc + CC - 1) / CC, g.K);
+        launch_pdl(kf_col_lean<N1, N2, CC>, grid, dim3(2 * CC * F::T), smem_col, st, true, g, A, B, mode, op,
                    scale);
     }
 };

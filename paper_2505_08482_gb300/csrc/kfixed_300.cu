@@ -5,7 +5,9 @@
 // 2 columns; 3 state staged in shared memory by TMA bulk copies; 4 all 15 x 20; 5 as 0 with 8 rows per CTA in the row passes; 6 as 0 with the segment recompute's row passes staged by TMA (fewer registers beside the adjoint); 7 as 5 with the column
 // passes on the three-level 5 x 10 x 6 transform (60 threads per column: 4 columns per CTA,
 // 8 in the forward sweep); 8 the same with 2 and 4 columns per CTA; 9 as 5 with 4-column tiles
-// for the column passes of the forward sweep too (more CTAs per SM when a launch has many waves).
+// for the column passes of the forward sweep too (more CTAs per SM when a launch has many waves);
+// 10 as 5 with column passes that form their multipliers where they use them (less shared memory:
+// faster for launches of many waves, slower in a chain of one-wave launches).
 #include "kfixed.cuh"
 
 namespace pat {
@@ -23,6 +25,8 @@ using PB = FixedImpl<15, 20, 8, 4, false>;   // persistent sweep: density rows
 using T4 = Col3Impl<5, 10, 6, 4>;            // three-level column passes
 using T8 = Col3Impl<5, 10, 6, 8>;
 using T2 = Col3Impl<5, 10, 6, 2>;
+using L4 = ColLeanImpl<20, 15, 4>;           // column passes, multipliers formed where used
+using L8 = ColLeanImpl<20, 15, 8>;
 }  // namespace
 
 const FixedOps* fixed_ops_300(int v) {
@@ -30,7 +34,7 @@ const FixedOps* fixed_ops_300(int v) {
                                    MixedImpl<A4, A8, B8, B8, C8>::ops(),
                                    MixedImpl<A4, A4, B4, B4, C8, S4, SB>::ops(),
                                    MixedImpl<T4, A8, B8, B8, T8>::ops(), MixedImpl<T2, A8, B8, B8, T4>::ops(),
-                                   MixedImpl<A4, A8, B8, B8, A4>::ops()};
+                                   MixedImpl<A4, A8, B8, B8, A4>::ops(), MixedImpl<L4, A8, B8, B8, L8>::ops()};
     return (v >= 0 && v < int(sizeof(ops) / sizeof(ops[0]))) ? &ops[v] : nullptr;
 }
 
