@@ -3,6 +3,8 @@
 // state is preloaded), and 8-column tiles for the column passes of the forward sweep, which
 // runs alone on the GPU; 1 all 12 x 12, 4 rows / 4 columns per CTA; 2 the same with 8 rows /
 // 2 columns; 3 state staged in shared memory by TMA bulk copies; 4 all 12 x 12; 5 as 0 with 8 rows per CTA in the row passes; 6 as 0 with the segment recompute's row passes staged by TMA (fewer registers beside the adjoint).
+// Variant 7: as 5 with column passes that form their multipliers where they use them (less
+// shared memory: for launches of many waves).
 #include "kfixed.cuh"
 
 namespace pat {
@@ -16,14 +18,16 @@ using C8 = FixedImpl<12, 12, 4, 8, false>;
 using B8 = FixedImpl<12, 12, 8, 2, false>;   // density rows, 8 rows per CTA
 using SB = FixedImpl<12, 12, 4, 4, true>;    // density rows staged by TMA (segment recompute)
 using PA = FixedImpl<12, 12, 8, 4, false>;   // persistent sweep: columns and velocity rows
+using L4 = ColLeanImpl<12, 12, 4>;   // column passes, multipliers formed where used
+using L8 = ColLeanImpl<12, 12, 8>;
 using PB = FixedImpl<12, 12, 8, 4, false>;   // persistent sweep: density rows
 }  // namespace
 
 const FixedOps* fixed_ops_144(int v) {
     static const FixedOps ops[] = {MixedImpl<A4, A4, B4, B4, C8>::ops(), A4::ops(), A8::ops(), S4::ops(), B4::ops(),
                                    MixedImpl<A4, A8, B8, B8, C8>::ops(),
-                                   MixedImpl<A4, A4, B4, B4, C8, S4, SB>::ops()};
-    return (v >= 0 && v < 7) ? &ops[v] : nullptr;
+                                   MixedImpl<A4, A4, B4, B4, C8, S4, SB>::ops(), MixedImpl<L4, A8, B8, B8, L8>::ops()};
+    return (v >= 0 && v < int(sizeof(ops) / sizeof(ops[0]))) ? &ops[v] : nullptr;
 }
 
 const SweepOps* sweep_ops_144() {
