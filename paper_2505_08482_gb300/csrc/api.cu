@@ -58,6 +58,7 @@ int run_steps(const Launch& L, const Ws& w, int n0, int n1, float* y, float* his
 
 int pat::forward_sweep(pat_plan_s* p, const float* c, const float* p0, float* y, const Ws& w, bool keep,
                        cudaStream_t st) {
+    NvtxRange nv("pat forward sweep");
     Launch L{p, st, true};
     RC(launch_medium(L, c, w.cg));
     PAT_CUDA(cudaMemsetAsync(y, 0, size_t(p->K) * p->nt * p->m * sizeof(float), st));
@@ -128,6 +129,7 @@ int run_adj(const Launch& L, const Ws& w, const float* r, int n_hi, int n_lo, bo
 // steps of segment j run on st; the two pressure-history buffers alternate.
 int reverse_sweep(pat_plan_s* p, const float* p0, const float* r, float* grad_p0, float* grad_c, const Ws& w,
                   bool hist_last_valid, cudaStream_t st) {
+    NvtxRange nv("pat reverse sweep");
     Launch L{p, st};
     const size_t f = size_t(p->K) * p->ng * p->ng;
     PAT_CUDA(cudaMemsetAsync(w.ubx, 0, 4 * f * sizeof(float), st));

@@ -9,6 +9,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/pat.h"
 #include "fft.cuh"
 
@@ -17,6 +19,15 @@ namespace pat {
 struct FixedOps;
 struct SweepOps;
 struct ClusterOps;
+
+// NVTX range on the host timeline for the lifetime of the object (profilers show the library's
+// calls, sweeps and multigrid levels by name; without a profiler attached it costs a branch)
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 void set_error(const char* fmt, ...);
 int cuda_fail(cudaError_t e, const char* where);
 

@@ -22,6 +22,8 @@
 // level or when the relative decrease of its J falls below rtol.
 #include <cuda_runtime.h>
 
+#include <cstdio>
+
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -504,6 +506,9 @@ int Batch::run() {
     int nprev = Nf;
     int rc = PAT_OK;
     for (int li = 0; li < cfg.nlevels && rc == PAT_OK; ++li) {
+        char nvname[64];
+        std::snprintf(nvname, sizeof(nvname), "pat_reconstruct level %d (n = %d)", li, cfg.levels[li]);
+        NvtxRange nv(nvname);
         rc = level(li, xprev.data(), nprev);
         if (rc != PAT_OK) break;
         for (int i = 0; i < ni; ++i) xprev[i] = I[i].x;

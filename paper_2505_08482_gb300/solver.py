@@ -391,6 +391,16 @@ def _rows(rep, rows):
                  ms=r.ms, Ec=r.Ec, Ep0=r.Ep0) for r in rows[:rep.count]]
 
 
+def write_report_jsonl(rows, path, **fields):
+    """Append one JSON line per L-BFGS iteration (level, iteration, J, |g|, step, trials, J after
+    the step, wall ms, E_c, E_p0 as returned by reconstruct / reconstruct_batched) to path, each
+    with the given extra fields (e.g. instance=3)."""
+    import json
+    with open(path, "a") as f:
+        for r in rows:
+            f.write(json.dumps(dict(fields, **r)) + "\n")
+
+
 def reconstruct_batched(cfg: ReconConfig, instances, stream=None, max_report=4096):
     """Several reconstructions sharing cfg, solved together (pat_reconstruct_batched).
 

@@ -87,3 +87,16 @@ def test_only_requested_gradients_are_returned():
     c = 1500 + torch.rand(3, 3)
     pat_forward(p0, c, plan).sum().backward()
     assert p0.grad is not None and c.grad is None
+
+
+def test_iteration_log_is_one_json_object_per_line(tmp_path):
+    import json
+    from paper_2505_08482_gb300.solver import write_report_jsonl
+    rows = [dict(level=0, it=0, J=2.0, gnorm=1.0, alpha=1.0, trials=1, J_new=1.5, ms=3.0, Ec=4.0, Ep0=50.0),
+            dict(level=1, it=0, J=1.5, gnorm=0.5, alpha=0.5, trials=2, J_new=1.0, ms=2.5, Ec=2.0, Ep0=30.0)]
+    p = tmp_path / "log.jsonl"
+    write_report_jsonl(rows, p, instance=7)
+    write_report_jsonl(rows[:1], p, instance=8)
+    lines = [json.loads(l) for l in open(p)]
+    assert [l["instance"] for l in lines] == [7, 7, 8]
+    assert lines[1]["level"] == 1 and lines[1]["Ec"] == 2.0 and lines[0]["J_new"] == 1.5

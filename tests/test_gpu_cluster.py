@@ -89,3 +89,27 @@ def test_cluster_form_only_on_its_grid_side():
     assert plan.cluster_capacity == 0
     with pytest.raises(B.PatError):
         plan.cluster = True
+
+
+def test_cluster_batched_plan_matches_launched_passes():
+    """Two instances with their own c in one batched plan (the medium of each data set is its
+    instance's): the cluster-resident sweep and gradient equal the launched passes'."""
+    n = 256
+    rng = ps.rng_for(36)
+    cs = np.stack([ps.ellipse_phantom(n, 3, rng), ps.ellipse_phantom(n, 5, rng)])
+    Ks = [1, 2]
+    p0 = np.stack([ps.vessel_p0(n, rng) for _ in range(sum(Ks))])
+    xy = ps.circle_sensors(n, 16, 1e-4, phase=0.4)
+    gp = grid_params(n, 40)
+    plan = gpu_plan(gp, xy, Ks, ckpt_every=9)
+    y_l = plan.forward(_dev(cs), _dev(p0)).cpu().numpy()
+    ym = _dev(y_l * 1.01 + 0.001)
+    wt = _dev(np.array([1.0, 0.5, 2.0]))
+    c0 = _dev(np.full((2, n, n), 1510.0))
+    J_l, a_l, b_l = [t.cpu().numpy() for t in plan.adjoint_grad(c0, _dev(0.5 * p0), ym, wt)]
+    plan.cluster = True
+    y_c = plan.forward(_dev(cs), _dev(p0)).cpu().numpy()
+    J_c, a_c, b_c = [t.cpu().numpy() for t in plan.adjoint_grad(c0, _dev(0.5 * p0), ym, wt)]
+    assert rel_l2(y_c, y_l) <= 1e-5
+    assert np.all(np.abs(J_c - J_l) <= 1e-5 * np.abs(J_l))
+    assert rel_l2(a_c, a_l) <= 1e-4 and rel_l2(b_c, b_l) <= 1e-4
