@@ -113,6 +113,8 @@ def parse():
     ap.add_argument("--roofline-k", type=int, default=0,
                     help="per-pass bandwidth of forward steps with this many data sets on the headline grid "
                          "(working set beyond L2 for K >= 64); uses --nt and --variant")
+    ap.add_argument("--cluster", action="store_true",
+                    help="with --roofline-k: forward sweeps in the cluster-resident form (pat_plan_set_cluster)")
     ap.add_argument("--prior-cost", action="store_true",
                     help="cost of the Ornstein-Uhlenbeck prior terms on the headline grid (9 fields)")
     ap.add_argument("--table2", action="store_true",
@@ -948,6 +950,8 @@ def run_roofline_k(args):
         plan.autotune(gradient=False)
     else:
         plan.variant = args.variant
+    if args.cluster:
+        plan.cluster = True
     f32 = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float32, device=dev)
     reps = -(-K // w.p0_true.shape[0])
     c, p0 = f32(w.c_true), f32(np.concatenate([w.p0_true] * reps)[:K])
@@ -959,7 +963,7 @@ def run_roofline_k(args):
     torch.cuda.synchronize()
     peak, peak_kind = measured_peaks()
     passes = {}
-    for cls in (3, 2, 4, 1):     # the four passes of a forward step
+    for cls in (() if args.cluster else (3, 2, 4, 1)):     # the four passes of a forward step
         B.check(L.pat_timing_enable(cls, nt + 8, 1), "pat_timing_enable")
         plan.forward(c, p0, y=y, stream=stream)
         tot, cnt = ctypes_read(L)
@@ -981,7 +985,8 @@ def run_roofline_k(args):
                       "unit": "GB/s", "n_gpus": 1, "dtype": "f32", "data": "synthetic",
                       "config": {"workload": f"vessels256 grid (Ng {ng}) with K={K} data sets, M={WL['M']}, "
                                              f"Nt={nt}", "K": K, "nt": nt},
-                      "variant": plan.variant, "peak": peak, "peak_kind": f"{peak_kind} hbm_gbs",
+                      "variant": plan.variant, "cluster_resident": bool(args.cluster),
+                      "peak": peak, "peak_kind": f"{peak_kind} hbm_gbs",
                       "passes": passes, "forward_ms": fwd_s * 1000.0,
                       "forward_gcell_steps_per_s": ng * ng * K * (nt - 1) / fwd_s / 1e9,
                       "kernel_source_hash": kernel_source_hash()}), flush=True)
