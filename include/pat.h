@@ -165,7 +165,9 @@ int pat_plan_persistent(pat_plan plan);
  * clusters (data sets) the current GPU runs at once (0 if none or no
  * cluster-resident stepping for the plan's grid side; PAT_EINVAL for a NULL
  * plan).  The launched passes are faster on GB300 at every K measured (the
- * cluster form is an option, off by default). */
+ * cluster form is an option, off by default).  With the persistent sweep also
+ * enabled, forward sweeps use the persistent sweep and segment recomputes the
+ * cluster form. */
 int pat_plan_set_cluster(pat_plan plan, int enable);
 int pat_plan_cluster(pat_plan plan);
 int pat_plan_cluster_capacity(pat_plan plan);
