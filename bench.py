@@ -113,6 +113,8 @@ def parse():
     ap.add_argument("--roofline-k", type=int, default=0,
                     help="per-pass bandwidth of forward steps with this many data sets on the headline grid "
                          "(working set beyond L2 for K >= 64); uses --nt and --variant")
+    ap.add_argument("--many-waves-k", type=int, default=64,
+                    help="data sets of the default line's many-waves pass measurement (0: none)")
     ap.add_argument("--cluster", action="store_true",
                     help="with --roofline-k: forward sweeps in the cluster-resident form (pat_plan_set_cluster)")
     ap.add_argument("--prior-cost", action="store_true",
@@ -641,6 +643,14 @@ def run_ours(args, rank, world, local_rank):
                                           f"host cores ({wall:.1f} s wall), scaled by (Nt-1) to Nt={WL['nt']}",
                                 "single_core_value": cpu_value(cpu, nt_s, K), "nproc": os.cpu_count(),
                                 "plain64_unscaled_s": oracle_plain64()}
+    if rank == 0 and world == 1 and args.many_waves_k > 0:
+        # the same passes with many waves of CTAs (working set beyond L2): the HBM-bound regime
+        mw = roofline_k(args.many_waves_k, 400, None, WL["ckpt_every"], 2, 3)
+        line["roofline"]["many_waves"] = {"workload": mw["config"]["workload"], "variant": mw["variant"],
+                                          "forward_gcell_steps_per_s": mw["forward_gcell_steps_per_s"],
+                                          "passes": mw["passes"], "peak": mw["peak"],
+                                          "timing": "CUDA events around every launch of a class in an eager "
+                                                    "forward sweep that runs alone; variant from the autotuner"}
     if rank == 0 and world == 1 and not args.no_ttr:
         line["time_to_rel_err"] = time_to_rel_err(args, dev)
         if not args.no_ws_sample:
@@ -921,6 +931,11 @@ def batch_sweep(n_inst, n_plain, iters, persistent):
 
 
 def run_roofline_k(args):
+    print(json.dumps(roofline_k(args.roofline_k, args.nt, args.variant, args.ckpt, args.warmup, args.steps,
+                                args.cluster)), flush=True)
+
+
+def roofline_k(K, nt, variant, ckpt, warmup, steps, cluster=False):
     """Per-pass achieved bandwidth of forward sweeps on the 300^2 grid with K data sets.
 
     At K = 8 the state and spectra of a step (about 30 MB) stay in L2 and the passes are
@@ -939,31 +954,32 @@ def run_roofline_k(args):
     torch.cuda.set_device(0)
     L = B.lib()
     w, _ = inputs(0)
-    n, K, nt = WL["n"], args.roofline_k, args.nt
+    n = WL["n"]
     P = pml_auto(n)
     dt = WL["cfl"] * WL["dx"] / WL["c_hi"]
     gs = GridSpec(n=n, pml=P, dx=WL["dx"], dt=dt, nt=nt, c_ref=WL["c_hi"], pml_alpha=WL["pml_alpha"],
                   c_bg=WL["c_bg"])
     ng = gs.ng
-    plan = Plan(gs, w.sensors, K, ckpt_every=args.ckpt, device=dev)
-    if args.variant is None:
+    plan = Plan(gs, w.sensors, K, ckpt_every=ckpt, device=dev)
+    if variant is None:
         plan.autotune(gradient=False)
     else:
-        plan.variant = args.variant
-    if args.cluster:
+        plan.variant = variant
+    if cluster:
         plan.cluster = True
     f32 = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float32, device=dev)
     reps = -(-K // w.p0_true.shape[0])
     c, p0 = f32(w.c_true), f32(np.concatenate([w.p0_true] * reps)[:K])
     y = torch.empty((K, nt, WL["M"]), dtype=torch.float32, device=dev)
     stream = torch.cuda.Stream(device=dev)
+    prev_stream = torch.cuda.current_stream(dev)
     torch.cuda.set_stream(stream)
-    for _ in range(max(args.warmup, 1)):
+    for _ in range(max(warmup, 1)):
         plan.forward(c, p0, y=y, stream=stream)
     torch.cuda.synchronize()
     peak, peak_kind = measured_peaks()
     passes = {}
-    for cls in (() if args.cluster else (3, 2, 4, 1)):     # the four passes of a forward step
+    for cls in (() if cluster else (3, 2, 4, 1)):     # the four passes of a forward step
         B.check(L.pat_timing_enable(cls, nt + 8, 1), "pat_timing_enable")
         plan.forward(c, p0, y=y, stream=stream)
         tot, cnt = ctypes_read(L)
@@ -976,20 +992,21 @@ def run_roofline_k(args):
                                          "frac": round(bpl / (us * 1e-6) / 1e9 / peak, 3)}
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    for _ in range(args.steps):
+    for _ in range(steps):
         plan.forward(c, p0, y=y, stream=stream)
     e1.record(stream)
     torch.cuda.synchronize()
-    fwd_s = e0.elapsed_time(e1) / 1000.0 / args.steps
-    print(json.dumps({"metric": f"per-pass achieved algorithmic HBM GB/s, forward sweep at K={K}",
+    fwd_s = e0.elapsed_time(e1) / 1000.0 / steps
+    torch.cuda.set_stream(prev_stream)
+    return {"metric": f"per-pass achieved algorithmic HBM GB/s, forward sweep at K={K}",
                       "unit": "GB/s", "n_gpus": 1, "dtype": "f32", "data": "synthetic",
                       "config": {"workload": f"vessels256 grid (Ng {ng}) with K={K} data sets, M={WL['M']}, "
                                              f"Nt={nt}", "K": K, "nt": nt},
-                      "variant": plan.variant, "cluster_resident": bool(args.cluster),
+                      "variant": plan.variant, "cluster_resident": bool(cluster),
                       "peak": peak, "peak_kind": f"{peak_kind} hbm_gbs",
                       "passes": passes, "forward_ms": fwd_s * 1000.0,
                       "forward_gcell_steps_per_s": ng * ng * K * (nt - 1) / fwd_s / 1e9,
-                      "kernel_source_hash": kernel_source_hash()}), flush=True)
+                      "kernel_source_hash": kernel_source_hash()}
 
 
 def run_prior_cost(args):
