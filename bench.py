@@ -226,8 +226,9 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-def stored_traffic(cls: int, src_hash: str):
-    """Per-launch DRAM bytes of kernel class cls from the committed ncu summary, if current."""
+def stored_traffic(cls: int, src_hash: str, key: str = "dram_bytes_per_launch_full"):
+    """Per-launch DRAM bytes (or another per-launch ncu figure) of kernel class cls from the
+    committed ncu summary, if current."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
@@ -235,7 +236,7 @@ def stored_traffic(cls: int, src_hash: str):
     e = d.get(str(cls))
     if not e or d.get("kernel_source_hash") != src_hash:
         return None
-    return e.get("dram_bytes_per_launch_full")
+    return e.get(key)
 
 
 # ---------------------------------------------------------------------------
@@ -598,6 +599,19 @@ def run_ours(args, rank, world, local_rank):
     achieved = bpl / (dom_us * 1e-6) / 1e9
     per_eval_ms = t_ms / args.steps
     cells = ng * ng * K * (nt - 1)
+    # the same launches against the instruction-issue peak (4 schedulers per SM, one warp
+    # instruction per cycle each, at the maximum SM clock), from the warp instructions per launch
+    # of the committed ncu capture
+    insts = stored_traffic(dom, src_hash, "warp_instructions_per_launch")
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    sm_max = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))).get("sm_max_mhz", 2070.0)) \
+        if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else 2070.0
+    issue_peak = 4.0 * sms * sm_max * 1e6
+    issue = None if insts is None else {
+        "bound": "alu", "unit": "warp instructions/s", "instructions_per_launch": insts,
+        "achieved": insts / (dom_us * 1e-6), "peak": issue_peak, "frac": insts / (dom_us * 1e-6) / issue_peak,
+        "peak_kind": f"4 schedulers x {sms} SMs x {sm_max:.0f} MHz (one warp instruction per cycle each)",
+        "source": "smsp__inst_executed.sum of the dominant pass (ncu, profiles/traffic.json)"}
     roof = {"bound": "hbm", "kernel": f"{B.KERNEL_CLASSES[dom]} ({dom_phase} sweep)", "achieved": achieved,
             "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": stored_traffic(dom, src_hash),
             "peak_kind": f"{peak_kind} hbm_gbs (burst copy)", "algorithmic_bytes_per_launch": bpl,
@@ -608,6 +622,7 @@ def run_ours(args, rank, world, local_rank):
                       "also end the programmatic launch overlap with the neighbouring kernels",
             "solo_us_per_launch": {f"{B.KERNEL_CLASSES[c]} ({ph})": round(v[0], 3) for (c, ph), v in solo.items()},
             "launches_per_eval": {B.KERNEL_CLASSES[c]: v for c, v in launches_per_eval.items()},
+            "issue": issue,
             "share_of_serialised_sum": round(dom_us * phase_launches[dom_key] / serial_us, 3),
             "share_note": "the dominant class's serialised time over the sum of every class's (solo launch time x "
                           "launches per evaluation): the quantity an ncu launch list of one evaluation gives",
