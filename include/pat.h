@@ -112,8 +112,8 @@ int pat_plan_shape(pat_plan plan, int* ninst, int* K);
 int pat_plan_ng(pat_plan plan);
 
 /* Kernel variants of a plan.  Grid sides with a compiled two-level FFT
- * (108, 144, 180, 200, 240, 300 = N1 x N2) have seven fixed-size variants,
- * all one launch per pass:
+ * (108, 144, 180, 200, 240, 300 = N1 x N2) have fixed-size variants (eight
+ * for 108-240, eleven for 300), all one launch per pass:
  *   0  column and velocity passes on the N1 x N2 factorisation, density
  *      passes on N2 x N1 (4 rows / 4 spectral columns per CTA); the column
  *      passes of the forward sweep, which runs alone on the GPU, take 8
@@ -126,7 +126,14 @@ int pat_plan_ng(pat_plan plan);
  *   5  as 0 with 8 rows per CTA in the row passes;
  *   6  as 0 with the segment recompute's row passes (which share the GPU
  *      with the adjoint) staged by TMA as in 3, so that they need fewer
- *      registers.
+ *      registers;
+ *   7  (108-240) as 5 with column passes that form their multipliers where
+ *      they use them (less shared memory: faster when a launch has many
+ *      waves of CTAs);
+ *   7, 8 (300) as 5 with the column passes on a three-level 5 x 10 x 6
+ *      register FFT (60 threads per column), 4 / 8 and 2 / 4 columns per CTA;
+ *   9  (300) as 5 with 4-column tiles in the forward sweep's column passes;
+ *   10 (300) as 5 with the column passes of 7 (108-240).
  * Every side also has the generic shared-memory Stockham passes (variant
  * -1).  All variants compute the same scheme.  A new plan uses variant 0
  * when it exists, else -1.  pat_plan_variants returns the number of
