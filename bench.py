@@ -89,6 +89,8 @@ def parse():
     ap.add_argument("--no-graphs", action="store_true", help="launch every kernel from the host (no CUDA graphs)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-ttr", action="store_true", help="skip the time-to-relative-error comparison")
+    ap.add_argument("--no-table2-sample", action="store_true",
+                    help="skip the simple-phantom K=4 vs K=1 reconstructions of the default line")
     ap.add_argument("--no-ws-sample", action="store_true",
                     help="skip the reduced warm-start comparison of the default line")
     ap.add_argument("--ws-sample-train", type=int, default=2048, help="training pairs of the reduced warm start")
@@ -670,6 +672,9 @@ def run_ours(args, rank, world, local_rank):
         line["time_to_rel_err"] = time_to_rel_err(args, dev)
         if not args.no_ws_sample:
             line["time_to_rel_err"]["warm_start"] = warm_start_sample(args)
+        if not args.no_table2_sample:
+            # the simple phantoms of Sec. 4.1 (K = 4 against K = 1, Table 2 trend)
+            line["table2_trend"] = table2(args.t2_iters)
         if args.batch_sample > 0:
             # the batched serving-style sweep on a reduced sample (all of it also solved one by one)
             b = batch_sweep(args.batch_sample, args.batch_sample, args.batch_iters, False)
@@ -1067,6 +1072,10 @@ def run_prior_cost(args):
 
 
 def run_table2(args):
+    print(json.dumps(table2(args.t2_iters)), flush=True)
+
+
+def table2(t2_iters):
     """Simple-phantom experiment (Sec. 4.1, Table 2 trend) on the paper's geometry.
 
     Data: 334 x 334 grid of 63.7 um over the 20 mm target plus its sensor layer, 236 sensors
@@ -1113,7 +1122,7 @@ def run_table2(args):
         row = {"U_c": U, "data_grid": f"{n_d}^2, dx {dx_d * 1e6:.1f} um, dt {dt_d * 1e9:.2f} ns, Nt {nt_d}"}
         for K in (4, 1):
             cfg = ReconConfig(levels=levels, L=L, dt_data=dt_d, nt_data=nt_d, sensors_xy=xy, K=K, cfl=0.3,
-                              c_lo=1300.0, c_hi=U, p0_lo=0.0, c_bg=1430.0, mem=20, iters=args.t2_iters, rtol=1e-5,
+                              c_lo=1300.0, c_hi=U, p0_lo=0.0, c_bg=1430.0, mem=20, iters=t2_iters, rtol=1e-5,
                               sigma_p0=2.5, prior_tau=1.5e-3, prior_eta_c=eta_c, prior_sigma_c=sig_c,
                               prior_eta_p0=5.0, prior_sigma_p0=2.5)
             t0 = time.perf_counter()
@@ -1126,12 +1135,12 @@ def run_table2(args):
         pe = paper[kind]
         row["paper_table2"] = {"E_c_K4": pe[0], "E_c_K1": pe[1], "E_p0_1_K4": pe[2], "E_p0_1_K1": pe[3]}
         out[kind] = row
-    print(json.dumps({"metric": "E_c and E_p0^1 (%) of the joint reconstruction, K=4 data sets vs K=1",
+    return {"metric": "E_c and E_p0^1 (%) of the joint reconstruction, K=4 data sets vs K=1",
                       "unit": "%", "n_gpus": 1, "dtype": "f32", "data": "synthetic",
                       "config": {"workload": "simple phantoms of Sec. 4.1 on the paper's 236-sensor square, data "
                                              "on a finer grid than every reconstruction level, levels "
-                                             f"{levels}, {args.t2_iters} iterations per level, OU prior"},
-                      "results": out, "total_s": time.perf_counter() - t_all}), flush=True)
+                                             f"{levels}, {t2_iters} iterations per level, OU prior"},
+                      "results": out, "total_s": time.perf_counter() - t_all}
 
 
 def run_warmstart(args):
