@@ -67,3 +67,25 @@ def test_line_search_failure_stops_and_reports():
 def test_projection():
     z = np.array([-2.0, 0.5, 3.0])
     assert np.all(L.project(z, np.array([-1.0, 0, 0]), np.array([1.0, 1, 2])) == [-1.0, 0.5, 2.0])
+
+
+def test_p7_reaches_the_exact_kkt_point():
+    """The box-constrained quadratic's minimiser in closed form: with the active set of the
+    solution, the free components solve A_ff x_f = b_f - A_fa x_a.  The projected gradient
+    (l = 0) reaches it to rounding; with l = 20 the Armijo test on J stops the iteration where
+    J's decrease falls below its rounding (x then within about 1e-8 of the minimiser, as is
+    scipy's L-BFGS-B)."""
+    A, b, lo, hi, f, fg = _quad()
+    ref = so.minimize(fg, np.zeros(50), jac=True, method="L-BFGS-B", bounds=list(zip(lo, hi)),
+                      options=dict(ftol=1e-16, gtol=1e-14, maxiter=5000)).x
+    act_lo, act_hi = ref <= lo + 1e-12, ref >= hi - 1e-12
+    free = ~(act_lo | act_hi)
+    x_star = np.where(act_lo, lo, np.where(act_hi, hi, 0.0))
+    x_star[free] = np.linalg.solve(A[np.ix_(free, free)], b[free] - A[np.ix_(free, ~free)] @ x_star[~free])
+    g = A @ x_star - b                    # KKT signs of the closed-form point
+    assert np.abs(g[free]).max() < 1e-12
+    assert np.all(g[act_lo] >= 0) and np.all(g[act_hi] <= 0)
+    assert np.abs(ref - x_star).max() < 1e-7
+    for mem, tol in ((0, 1e-11), (20, 1e-7)):
+        res = L.projected_lbfgs(f, fg, np.zeros(50), lo, hi, np.full(50, 2.0), mem=mem, max_iter=2000, rtol=0.0)
+        assert np.abs(res.x - x_star).max() < tol, (mem, np.abs(res.x - x_star).max())
