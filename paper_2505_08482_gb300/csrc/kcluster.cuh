@@ -153,7 +153,7 @@ struct ClusterImpl {
 
     // Column phase: mode 0 (G): field 0 -> (MX, MY) x it into fields 0, 1 of the row buffers;
     // mode 1 (D): fields 0, 1 -> (MX f0, MY f1).  op: 0 G factors, 1 D factors.
-    static __device__ __forceinline__ void col_phase(int mode, int op, float scale, int kx0, int nc) {
+    static __device__ __noinline__ void col_phase(int mode, int op, float scale, int kx0, int nc) {
         const int tid = opaque(int(threadIdx.x));
         kx0 = opaque(kx0);
         const int f = tid / (CMAX * TC), tl = tid - f * (CMAX * TC);
@@ -224,7 +224,7 @@ struct ClusterImpl {
     // sequence q's real part -> row ya(q) of field fa, imaginary part -> row yb(q) of field fb
     // (pairs: rows y0 + 2q and y0 + 2q + 1 of field 0, the second only when below y0 + nr; else
     // row y0 + q of fields 0 and 1), stored into the owners' column buffers
-    static __device__ __forceinline__ void row_finish_scatter(int y0, int nr, bool pairs) {
+    static __device__ __noinline__ void row_finish_scatter(int y0, int nr, bool pairs) {
         const int t = threadIdx.x;
         const int q = t / TR, ridx = t - q * TR;
         const int nseq = pairs ? (nr + 1) / 2 : nr;
@@ -256,7 +256,7 @@ struct ClusterImpl {
 
     // sensors of one level from the pressure rows P, then (scatter) the first step of the row R2C
     // of p, two rows per complex transform (P shares the row buffer with the transform scratch)
-    static __device__ __forceinline__ void p_sensors_pairs(const Sens& se_, int y0, int nr, bool scatter) {
+    static __device__ __noinline__ void p_sensors_pairs(const Sens& se_, int y0, int nr, bool scatter) {
         const int t = threadIdx.x;
         const int r = t / TR, ridx = t - r * TR;
         const float* P = s_P();
@@ -283,12 +283,12 @@ struct ClusterImpl {
         row_forward_a(r, ridx, act, av);
     }
 
-    // The phases of a step, cut where everything a phase hands on is in shared memory, and run as
-    // the cases of one switch over the sub-phase index (inlined one after the other into the
-    // time loop, the register allocation of the phases overlaps and spills).
+    // The phases of a step, cut where everything a phase hands on is in shared memory, run as the
+    // cases of one switch over the sub-phase index, each outlined (its own register allocation:
+    // inlined into one time loop, the allocations of the phases overlap and spill).
     // velocity rows, first part: inverse row FFTs, u <- a'(a' u - g) (init: u = g / 2 first),
     // first step of the R2C of u
-    static __device__ __forceinline__ void phase_u(int y0, int nr, int init_u) {
+    static __device__ __noinline__ void phase_u(int y0, int nr, int init_u) {
         const int t = threadIdx.x;
         const int r = t / TR, ridx = t - r * TR;
         const bool rowt = r < nr, aact = rowt && ridx < AT;
@@ -318,7 +318,7 @@ struct ClusterImpl {
     // density rows, first part: inverse row FFTs, rho <- a(a rho - g), p = c^2 (rho_x + rho_y)
     // into P and the history row hr (or null), the state into the checkpoint rows ck (or null,
     // f4 apart)
-    static __device__ __forceinline__ void phase_rho(int y0, int nr, float* hr, float* ck, size_t f4) {
+    static __device__ __noinline__ void phase_rho(int y0, int nr, float* hr, float* ck, size_t f4) {
         const int t = threadIdx.x;
         const int r = t / TR, ridx = t - r * TR;
         const bool rowt = r < nr, aact = rowt && ridx < AT;
