@@ -473,3 +473,91 @@ def reconstruct(cfg: ReconConfig, y_meas, w, c_init, p0_init=None, stream=None, 
         B.check(B.lib().pat_reconstruct(ctypes.byref(c_cfg), _ptr(y_meas), _ptr(w), _ptr(c), _ptr(p0),
                                         ctypes.byref(rep), _stream(stream)), "pat_reconstruct")
     return c, p0, _rows(rep, rows), int(rep.status), float(rep.total_ms)
+
+
+def _fingerprint(cfg: ReconConfig, tensors) -> str:
+    """Hash of the configuration and of the inputs a resumed run must share with the first."""
+    import dataclasses
+    import hashlib
+    import json
+    h = hashlib.sha256()
+    fields = {k: (np.asarray(v, dtype=np.float64).tolist() if k == "sensors_xy" else
+                  [int(x) for x in v] if k == "levels" else v)
+              for k, v in dataclasses.asdict(cfg).items()}
+    h.update(json.dumps(fields, sort_keys=True).encode())
+    for t in tensors:
+        a = np.ascontiguousarray(t.detach().cpu().numpy())
+        h.update(str(a.shape).encode())
+        h.update(a.tobytes())
+    return h.hexdigest()
+
+
+_ROW_FIELDS = ("level", "it", "J", "gnorm", "alpha", "trials", "J_new", "ms", "Ec", "Ep0")
+
+
+def reconstruct_resumable(cfg: ReconConfig, y_meas, w, c_init, state_path, p0_init=None, stop_after_level=None,
+                          stream=None, max_report=4096):
+    """Joint reconstruction that can stop after any multigrid level and continue later from a host file.
+
+    The schedule runs one level per pat_reconstruct call (levels=(N_l,)).  A level boundary is
+    where the method itself ends one optimisation and starts the next from the prolonged point
+    with an empty L-BFGS memory (Sec. 3.1), so the state there is the iterate alone: no curvature
+    pairs, and no random numbers (the reconstruction draws none).  After each level the state
+    (levels done, c and p0 on that level's grid, the report rows so far, status, wall time and a
+    fingerprint of cfg and the inputs) is written to ``state_path`` (an .npz, replaced
+    atomically).  Called with an existing state file it checks the fingerprint (ValueError if
+    cfg or any input differs) and continues with the next level: the first level's initial
+    guess and every level's start are the same bilinear transfers (pat_prolong) that
+    pat_reconstruct applies, and resampling onto the same grid inside the call is the identity,
+    so with the kernel variant fixed (cfg.autotune off) the result is bit-identical to one
+    pat_reconstruct over all levels.  ``stop_after_level`` = l returns after level l (an
+    interruption at a level boundary).
+
+    Returns (c, p0, report rows, status, total_ms, levels_done); c and p0 are on the grid of the
+    last level done (the finest once levels_done == len(cfg.levels)).
+    """
+    import dataclasses
+    import io
+    import json
+    import os
+    levels = [int(v) for v in cfg.levels]
+    N = levels[-1]
+    K = int(cfg.K)
+    dev = y_meas.device
+    p0_in = torch.zeros((K, N, N), dtype=torch.float32, device=dev) if p0_init is None else p0_init
+    _f32(c_init, (N, N), "c_init", dev)
+    _f32(p0_in, (K, N, N), "p0_init", dev)
+    fp = _fingerprint(cfg, (y_meas, w, c_init, p0_in))
+    done, rows, status, total = 0, [], 0, 0.0
+    c, p0 = c_init.detach().clone().contiguous(), p0_in.detach().clone().contiguous()
+    if os.path.exists(state_path):
+        with np.load(state_path, allow_pickle=False) as z:
+            meta = json.loads(str(z["meta"]))
+            if meta["fingerprint"] != fp:
+                raise ValueError(f"{state_path}: saved by a run with another configuration or other inputs")
+            done, status, total = int(meta["levels_done"]), int(meta["status"]), float(meta["total_ms"])
+            rows = [dict(zip(_ROW_FIELDS, r)) for r in meta["rows"]]
+            c = torch.as_tensor(z["c"], device=dev).contiguous()
+            p0 = torch.as_tensor(z["p0"], device=dev).contiguous()
+    last = len(levels) - 1 if stop_after_level is None else min(int(stop_after_level), len(levels) - 1)
+    for li in range(done, last + 1):
+        n_l = levels[li]
+        c_start = prolong(c.view(1, *c.shape), n_l, stream=stream)[0].contiguous()
+        p0_start = prolong(p0, n_l, stream=stream)
+        one = dataclasses.replace(cfg, levels=(n_l,))
+        c, p0, r, st, ms = reconstruct(one, y_meas, w, c_start, p0_start, stream=stream, max_report=max_report)
+        for row in r:
+            row["level"] = li
+        rows += r
+        status = st if st != 0 else status
+        total += ms
+        done = li + 1
+        meta = {"fingerprint": fp, "levels_done": done, "levels": levels, "status": status, "total_ms": total,
+                "rows": [[row[k] for k in _ROW_FIELDS] for row in rows]}
+        buf = io.BytesIO()
+        np.savez(buf, c=c.cpu().numpy(), p0=p0.cpu().numpy(), meta=np.array(json.dumps(meta)))
+        tmp = f"{state_path}.tmp{os.getpid()}"
+        with open(tmp, "wb") as f:
+            f.write(buf.getvalue())
+        os.replace(tmp, state_path)
+    return c, p0, rows, status, total, done
