@@ -66,7 +66,7 @@ def bytes_per_cell(cls: int, ng: int, n: int, ckpt_hist: bool = True) -> float:
 FWD_BYTES = 36.5
 GRAD_BYTES = 125.0
 
-KERNEL_FILES = ("fft.cuh", "fft2l.cuh", "geo.cuh", "sync.cuh", "kfixed.cuh", "kfixed_300.cu", "kernels.cu", "api.cu")
+KERNEL_FILES = ("fft.cuh", "fft2l.cuh", "geo.cuh", "sync.cuh", "dcheck.cuh", "kfixed.cuh", "kfixed_300.cu", "kernels.cu", "api.cu")
 
 
 def kernel_source_hash() -> str:

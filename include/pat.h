@@ -245,8 +245,9 @@ int pat_forward_noalloc(pat_plan plan, const float* d_c, const float* d_p0, floa
 
 /* Status of the last pat_forward_noalloc with this plan, read from the
  * static array after synchronising the stream: *h_flag gets PAT_STATUS_WAIT
- * if a staged row pass (variant 3) gave up its bounded wait, so that the
- * traces of that call are invalid; 0 otherwise.  The array is shared, so
+ * if a staged row pass (variant 3) gave up its bounded wait, and (debug
+ * build) PAT_STATUS_BOUNDS if a bounds check failed, so that the traces of
+ * that call are invalid; 0 otherwise.  The array is shared, so
  * the answer concerns the last allocation-free call of any plan. */
 int pat_forward_noalloc_status(pat_plan plan, int* h_flag, void* stream);
 
@@ -283,6 +284,25 @@ int pat_vjp(pat_plan plan, const float* d_c, const float* d_p0, const float* d_y
 #define PAT_STATUS_NONFINITE 1
 #define PAT_STATUS_WAIT 2
 #define PAT_STATUS_QUEUE 4
+/* Bit 4 (PAT_STATUS_BOUNDS), debug build only (pat_debug_bounds() == 1): a
+ * device-side bounds check of the last forward / gradient / vjp failed on an
+ * index taken from run-time data (a sensor stencil entry, the time step, the
+ * history slot); the access was skipped or redirected to an index in range,
+ * so the results of that call are invalid. */
+#define PAT_STATUS_BOUNDS 16
+
+/* 1 if this library was built with the device-side bounds checks
+ * (-DPAT_DEBUG_BOUNDS: libpat_debug.so), 0 for the release build, whose
+ * checks compile to nothing.  Not from the paper: a debugging aid. */
+int pat_debug_bounds(void);
+
+/* Self-test of the bounds check behind PAT_STATUS_BOUNDS: one CTA checks an
+ * index one past the end of a shared-memory array (which has one spare
+ * element, so the guarded store stays in bounds whichever build runs it).
+ * The debug build ORs PAT_STATUS_BOUNDS into the device int *d_status and
+ * skips the store; the release build leaves *d_status unchanged.  PAT_EINVAL
+ * for a NULL pointer. */
+int pat_selftest_bounds(int* d_status, void* stream);
 
 /* Self-test of the bounded wait behind PAT_STATUS_WAIT: launches one CTA on
  * the stream whose threads wait for an mbarrier phase that never completes

@@ -10,7 +10,7 @@ import ctypes
 import os
 from ctypes import POINTER, c_char_p, c_double, c_int, c_size_t, c_void_p
 
-from ._build import LIB
+from ._build import LIB, LIB_DEBUG
 
 PAT_OK = 0
 PAT_EINVAL = -1
@@ -35,6 +35,7 @@ PAT_STATUS_NONFINITE = 1
 PAT_STATUS_WAIT = 2
 PAT_STATUS_QUEUE = 4
 PAT_STATUS_TC05 = 8
+PAT_STATUS_BOUNDS = 16
 
 
 class PatGrid(ctypes.Structure):
@@ -93,6 +94,8 @@ SIGNATURES = {
     "pat_status": (c_int, [c_void_p, c_void_p, POINTER(c_int), c_void_p]),
     "pat_selftest_wait": (c_int, [c_void_p, ctypes.c_uint, c_void_p]),
     "pat_selftest_queue": (c_int, [c_void_p, c_void_p, ctypes.c_uint, c_void_p]),
+    "pat_debug_bounds": (c_int, []),
+    "pat_selftest_bounds": (c_int, [c_void_p, c_void_p]),
     "pat_plan_set_persistent": (c_int, [c_void_p, c_int]),
     "pat_plan_persistent": (c_int, [c_void_p]),
     "pat_plan_set_cluster": (c_int, [c_void_p, c_int]),
@@ -134,17 +137,25 @@ SIGNATURES = {
 _lib = None
 
 
+def lib_path() -> str:
+    """libpat.so, or libpat_debug.so (the bounds-checked build) when PAT_DEBUG_BOUNDS=1."""
+    return LIB_DEBUG if os.environ.get("PAT_DEBUG_BOUNDS") == "1" else LIB
+
+
 def lib() -> ctypes.CDLL:
-    """Load libpat.so (built in-tree by ``build()``); raises if it is missing."""
+    """Load libpat.so (built in-tree by ``build()``; libpat_debug.so from ``build(debug=True)`` when the
+    environment has PAT_DEBUG_BOUNDS=1); raises if it is missing."""
     global _lib
     if _lib is None:
-        if not os.path.exists(LIB):
-            raise RuntimeError(f"libpat.so not found at {LIB}: run paper_2505_08482_gb300.build() first")
+        path = lib_path()
+        if not os.path.exists(path):
+            raise RuntimeError(f"{os.path.basename(path)} not found at {path}: run "
+                               f"paper_2505_08482_gb300.build({'debug=True' if path == LIB_DEBUG else ''}) first")
         try:
             import torch  # noqa: F401  (loads the CUDA runtime first)
         except ImportError:
             pass
-        L = ctypes.CDLL(LIB)
+        L = ctypes.CDLL(path)
         for name, (res, args) in SIGNATURES.items():
             fn = getattr(L, name)
             fn.restype = res

@@ -3,6 +3,12 @@
 Each ``csrc/*.cu`` translation unit is compiled in parallel into
 ``_build/`` and linked into ``paper_2505_08482_gb300/_lib/libpat.so``.  The
 library is rebuilt when a source or header is newer than it.
+
+``build(debug=True)`` builds the same sources with ``-DPAT_DEBUG_BOUNDS``
+into ``_build_debug/`` and ``_lib/libpat_debug.so``: device-side bounds
+checks on the indices that come from run-time data, reported through the
+status word (PAT_STATUS_BOUNDS).  The binding loads it instead of
+``libpat.so`` when the environment has ``PAT_DEBUG_BOUNDS=1``.
 """
 from __future__ import annotations
 
@@ -18,6 +24,8 @@ CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIBDIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(LIBDIR, "libpat.so")
+BUILD_DEBUG = os.path.join(PKG, "_build_debug")
+LIB_DEBUG = os.path.join(LIBDIR, "libpat_debug.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -37,26 +45,30 @@ def _deps():
         [os.path.join(ROOT, "include", "pat.h")]
 
 
-def is_stale() -> bool:
-    if not os.path.exists(LIB):
+def is_stale(debug: bool = False) -> bool:
+    lib = LIB_DEBUG if debug else LIB
+    if not os.path.exists(lib):
         return True
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return any(os.path.getmtime(d) > t for d in _deps())
 
 
-def build(force: bool = False, verbose: bool = False, extra_flags=None) -> str:
-    """Build libpat.so if needed and return its path."""
-    if not force and not is_stale():
-        return LIB
+def build(force: bool = False, verbose: bool = False, extra_flags=None, debug: bool = False) -> str:
+    """Build libpat.so (debug: libpat_debug.so with the bounds checks) if needed and return its path."""
+    lib = LIB_DEBUG if debug else LIB
+    bdir = BUILD_DEBUG if debug else BUILD
+    if not force and not is_stale(debug):
+        return lib
     nvcc = _nvcc()
-    os.makedirs(BUILD, exist_ok=True)
+    os.makedirs(bdir, exist_ok=True)
     os.makedirs(LIBDIR, exist_ok=True)
     flags = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--cudart", "shared",
-                    "-I", os.path.join(ROOT, "include")] + list(extra_flags or [])
+                    "-I", os.path.join(ROOT, "include")] + (["-DPAT_DEBUG_BOUNDS"] if debug else []) + \
+        list(extra_flags or [])
     objs = []
     cmds = []
     for src in _sources():
-        obj = os.path.join(BUILD, os.path.basename(src) + ".o")
+        obj = os.path.join(bdir, os.path.basename(src) + ".o")
         objs.append(obj)
         cmds.append([nvcc] + flags + ["-c", src, "-o", obj])
 
@@ -70,8 +82,8 @@ def build(force: bool = False, verbose: bool = False, extra_flags=None) -> str:
         for out in ex.map(run, cmds):
             if verbose and out.strip():
                 print(out)
-    link = [nvcc] + ARCH + ["-shared", "--cudart", "shared", "-o", LIB + ".tmp"] + objs + \
+    link = [nvcc] + ARCH + ["-shared", "--cudart", "shared", "-o", lib + ".tmp"] + objs + \
         ["-Xlinker", "-rpath,/usr/local/cuda/lib64"]
     run(link)
-    os.replace(LIB + ".tmp", LIB)
-    return LIB
+    os.replace(lib + ".tmp", lib)
+    return lib

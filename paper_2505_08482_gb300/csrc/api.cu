@@ -381,6 +381,6 @@ extern "C" int pat_status(pat_plan p, const void* ws, int* h_flag, void* stream)
     int f[2] = {0, 0};
     PAT_CUDA(cudaMemcpyAsync(f, b + p->o_flag, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
     PAT_CUDA(cudaStreamSynchronize(st));
-    *h_flag = (f[0] ? PAT_STATUS_NONFINITE : 0) | (f[1] & (PAT_STATUS_WAIT | PAT_STATUS_QUEUE));
+    *h_flag = (f[0] ? PAT_STATUS_NONFINITE : 0) | (f[1] & (PAT_STATUS_WAIT | PAT_STATUS_QUEUE | PAT_STATUS_BOUNDS));
     return PAT_OK;
 }

@@ -20,6 +20,7 @@
 
 #include "pat_internal.h"
 #include "geo.cuh"
+#include "dcheck.cuh"
 #include "kfixed.cuh"
 #include "kcluster.cuh"
 
@@ -41,6 +42,7 @@ __global__ void __launch_bounds__(256) k_row_rho(Geo g, float2* __restrict__ A, 
     const int k = blockIdx.y;
     const int y0 = blockIdx.x * R;
     const int nr = min(R, ng - y0);
+    const int hslot = hist ? in_range_or_zero(hist_slot, g.s_eff, g.status) : 0;
     float2* tw = sm;
     float2* z = sm + ng;
     float2* w = z + R * ng;
@@ -71,7 +73,7 @@ __global__ void __launch_bounds__(256) k_row_rho(Geo g, float2* __restrict__ A, 
             const float c = cg[size_t(yy) * ng + x];
             const float pv = c * c * (rxn + ryn);
             pr[i] = pv;
-            if (hist) hist[(size_t(k) * g.s_eff + hist_slot) * ng * ng + size_t(yy) * ng + x] = pv;
+            if (hist) hist[(size_t(k) * g.s_eff + hslot) * ng * ng + size_t(yy) * ng + x] = pv;
         }
         freeb = res;
     } else {
@@ -92,7 +94,7 @@ __global__ void __launch_bounds__(256) k_row_rho(Geo g, float2* __restrict__ A, 
                 pv = c * c * (rx[o] + ry[o]);
             }
             pr[i] = pv;
-            if (hist) hist[(size_t(k) * g.s_eff + hist_slot) * ng * ng + size_t(yy) * ng + x] = pv;
+            if (hist) hist[(size_t(k) * g.s_eff + hslot) * ng * ng + size_t(yy) * ng + x] = pv;
         }
         freeb = z;
     }
@@ -103,6 +105,9 @@ __global__ void __launch_bounds__(256) k_row_rho(Geo g, float2* __restrict__ A, 
             const int2 se = g.sent[e];
             const float4 sw = g.sentw[e];
             const int r = int(sw.w) - y0;
+            if (!(in_range(r, nr, g.status) && in_range(se.y + 1, ng, g.status) && in_range(se.x, g.m, g.status) &&
+                  in_range(tstep, g.nt, g.status)))
+                continue;
             const float v = sw.z * (sw.x * pr[r * ng + se.y] + sw.y * pr[r * ng + se.y + 1]);
             // at most two adds (rows iy, iy+1) onto a zeroed sample: order-independent
             atomicAdd(&y[(size_t(k) * g.nt + tstep) * g.m + se.x], v);
@@ -269,10 +274,11 @@ __device__ __forceinline__ void scatter_rows(const Geo& g, float* pb, const floa
                                              int tstep, int y0, int nr) {
     if (threadIdx.x < nr) {
         const int r = threadIdx.x, yy = y0 + r;
-        const float* rv = resid + (size_t(k) * g.nt + tstep) * g.m;
+        const float* rv = resid + (size_t(k) * g.nt + in_range_or_zero(tstep, g.nt, g.status)) * g.m;
         for (int e = g.srow[yy]; e < g.srow[yy + 1]; ++e) {
             const int2 se = g.sent[e];
             const float4 sw = g.sentw[e];
+            if (!(in_range(se.x, g.m, g.status) && in_range(se.y + 1, g.ng, g.status))) continue;
             const float v = rv[se.x] * sw.z;
             pb[r * g.ng + se.y] += sw.x * v;
             pb[r * g.ng + se.y + 1] += sw.y * v;
@@ -311,7 +317,7 @@ __global__ void __launch_bounds__(256) k_row_adj_rho(Geo g, float2* __restrict__
     scatter_rows(g, pb, resid, k, tstep, y0, nr);
     const size_t kf = size_t(k) * ng * ng;
     cg = medium_of(g, cg, k);
-    const float* hp = hist + (size_t(k) * g.s_eff + hist_slot) * ng * ng;
+    const float* hp = hist + (size_t(k) * g.s_eff + in_range_or_zero(hist_slot, g.s_eff, g.status)) * ng * ng;
     for (int i = threadIdx.x; i < nr * ng; i += blockDim.x) {
         const int r = i / ng, x = i - r * ng, yy = y0 + r;
         const size_t o = kf + size_t(yy) * ng + x;

@@ -35,6 +35,7 @@
 #include <cstdint>
 #include <type_traits>
 
+#include "dcheck.cuh"
 #include "fft2l.cuh"
 #include "geo.cuh"
 #include "sync.cuh"
@@ -637,7 +638,9 @@ __device__ __forceinline__ void row_rho_body(const Geo& g, const Ctx& ctx, float
     if constexpr (STAGE) mbar_wait(mb, 0, g.status);
     if (aact) {
         float* Pr = P + r * PN;
-        float* hr = hist ? hist + (size_t(k) * g.s_eff + hist_slot) * N * N + size_t(yy) * N : nullptr;
+        float* hr = hist ? hist + (size_t(k) * g.s_eff + in_range_or_zero(hist_slot, g.s_eff, g.status)) * N * N +
+                               size_t(yy) * N
+                         : nullptr;
         float2 a[N1];
         if (mode == 0) {
             F::inv_a_load(a, idx, Z0 + r * ZR);
@@ -695,6 +698,9 @@ __device__ __forceinline__ void row_rho_body(const Geo& g, const Ctx& ctx, float
             const int2 se = g.sent[e];
             const float4 sw = g.sentw[e];
             const int rr = int(sw.w) - y0;
+            if (!(in_range(rr, nr, g.status) && in_range(se.y + 1, N, g.status) && in_range(se.x, g.m, g.status) &&
+                  in_range(tstep, g.nt, g.status)))
+                continue;
             const float v = sw.z * (sw.x * P[rr * PN + se.y] + sw.y * P[rr * PN + se.y + 1]);
             // at most two adds (rows iy, iy+1) onto a zeroed sample: order-independent
             atomicAdd(&y[(size_t(k) * g.nt + tstep) * g.m + se.x], v);
@@ -815,25 +821,27 @@ __global__ void __launch_bounds__(RR * Fft2<N1, N2>::T) kf_row_adj_rho(Geo g, fl
     __shared__ float s_ewa[kMaxEnt], s_ewb[kMaxEnt];
     const int e0 = g.srow[y0], e1 = g.srow[y0 + nr];
     const bool ent_pre = e1 - e0 <= kMaxEnt;
-    const float* rv = resid + (size_t(k) * g.nt + tstep) * g.m;
+    const float* rv = resid + (size_t(k) * g.nt + in_range_or_zero(tstep, g.nt, g.status)) * g.m;
     if (ent_pre)
         for (int e = e0 + int(threadIdx.x); e < e1; e += blockDim.x) {
             const int2 se = g.sent[e];
             const float4 sw = g.sentw[e];
-            const float v = rv[se.x] * sw.z;
-            s_ecol[e - e0] = se.y;
+            const bool ok = in_range(se.x, g.m, g.status) && in_range(se.y + 1, N, g.status);
+            const float v = ok ? rv[se.x] * sw.z : 0.f;
+            s_ecol[e - e0] = ok ? se.y : 0;
             s_ewa[e - e0] = sw.x * v;
             s_ewb[e - e0] = sw.y * v;
         }
     // The pressure history is written by the segment recompute on the other stream, which this
     // segment's first kernel waits for through an event (a full dependency), or by the forward
     // sweep: never by the kernel just before, so it is fetched before the wait as well.
-    const float* hr = hist + (size_t(k) * g.s_eff + hist_slot) * N * N + size_t(yy) * N;
+    const int hslot = in_range_or_zero(hist_slot, g.s_eff, g.status);
+    const float* hr = hist + (size_t(k) * g.s_eff + hslot) * N * N + size_t(yy) * N;
     if constexpr (STAGE) {
         if (threadIdx.x == 0) {
             const uint32_t bytes = rows_bytes<N>(nr);
             mbar_arrive_expect(mb, bytes);
-            bulk_load(Sh, hist + (size_t(k) * g.s_eff + hist_slot) * N * N + size_t(y0) * N, bytes, mb);
+            bulk_load(Sh, hist + (size_t(k) * g.s_eff + hslot) * N * N + size_t(y0) * N, bytes, mb);
         }
     } else if (aact) {
         static_for<0, N1>([&](auto I) { hv[decltype(I)::value] = hr[idx + N2 * decltype(I)::value]; });
@@ -872,6 +880,7 @@ __global__ void __launch_bounds__(RR * Fft2<N1, N2>::T) kf_row_adj_rho(Geo g, fl
             for (int e = ea; e < eb; ++e) {
                 const int2 se = g.sent[e];
                 const float4 sw = g.sentw[e];
+                if (!(in_range(se.x, g.m, g.status) && in_range(se.y + 1, N, g.status))) continue;
                 const float v = rv[se.x] * sw.z;
                 PB[rr * PN + se.y] += sw.x * v;
                 PB[rr * PN + se.y + 1] += sw.y * v;

@@ -75,7 +75,7 @@ extern "C" int pat_forward_noalloc(pat_plan p, const float* c, const float* p0, 
 }
 
 // Status word of the last pat_forward_noalloc of this plan: the bounded-wait bit that the
-// staged row passes set in the scratch's flag region (the forward sets no other bit).
+// staged row passes set in the scratch's flag region, and the bounds bit of the debug build.
 extern "C" int pat_forward_noalloc_status(pat_plan p, int* h_flag, void* stream) {
     if (!p || !h_flag) {
         pat::set_error("pat_forward_noalloc_status: null argument");
@@ -91,6 +91,6 @@ extern "C" int pat_forward_noalloc_status(pat_plan p, int* h_flag, void* stream)
     PAT_CUDA(cudaMemcpyAsync(f, static_cast<const char*>(scratch) + p->o_flag, 2 * sizeof(int),
                              cudaMemcpyDeviceToHost, st));
     PAT_CUDA(cudaStreamSynchronize(st));
-    *h_flag = f[1] & (PAT_STATUS_WAIT | PAT_STATUS_QUEUE);
+    *h_flag = f[1] & (PAT_STATUS_WAIT | PAT_STATUS_QUEUE | PAT_STATUS_BOUNDS);
     return PAT_OK;
 }

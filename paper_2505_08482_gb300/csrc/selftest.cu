@@ -2,9 +2,12 @@
 // CTA waits for a phase that nothing completes: no arrival, no copy in flight) and the
 // dependency wait of the persistent sweep (one CTA waits for a work item that no CTA
 // completes).  Each gives up after the given time and reports it in the status word,
-// as a pass whose copies never land or whose producer never finishes would.
+// as a pass whose copies never land or whose producer never finishes would.  Also the
+// self-test of the debug build's bounds check (an index one past the end of an array
+// that has a spare element, so the guarded store is in bounds in either build).
 #include <cuda_runtime.h>
 
+#include "dcheck.cuh"
 #include "kfixed.cuh"
 #include "pat_internal.h"
 
@@ -24,10 +27,27 @@ __global__ void k_selftest_queue(int* queue, int* status, unsigned long long lim
     ctx.input_ready();   // waits for one item of data set 0 that nothing produces
 }
 
+__global__ void k_selftest_bounds(int* status) {
+    __shared__ float buf[3];
+    const int i = 2;   // one past the end of the checked range [0, 2)
+    if (in_range(i, 2, status)) buf[i] = 1.f;
+    __syncthreads();
+}
+
 }  // namespace
 }  // namespace pat
 
 using namespace pat;
+
+extern "C" int pat_debug_bounds(void) { return kDebugBounds ? 1 : 0; }
+
+extern "C" int pat_selftest_bounds(int* d_status, void* stream) {
+    if (!d_status) { set_error("pat_selftest_bounds: null status"); return PAT_EINVAL; }
+    count_launch();
+    k_selftest_bounds<<<1, 32, 0, static_cast<cudaStream_t>(stream)>>>(d_status);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? PAT_OK : cuda_fail(e, "k_selftest_bounds");
+}
 
 extern "C" int pat_selftest_wait(int* d_status, unsigned timeout_us, void* stream) {
     if (!d_status) { set_error("pat_selftest_wait: null status"); return PAT_EINVAL; }

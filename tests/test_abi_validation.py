@@ -82,6 +82,8 @@ def test_selftest_and_prior_arguments(L, B):
     assert L.pat_selftest_wait(None, 1000, None) == B.PAT_EINVAL
     assert L.pat_selftest_wait(FAKE, 0, None) == B.PAT_EINVAL
     assert L.pat_selftest_wait(FAKE, 2000000, None) == B.PAT_EINVAL
+    assert L.pat_selftest_bounds(None, None) == B.PAT_EINVAL
+    assert L.pat_debug_bounds() == 0   # the release library: checks compiled out
     out = ctypes.c_void_p()
     assert L.pat_prior_create(64, 1e-4, 1.5e-3, 4, None) == B.PAT_EINVAL
     for n, dx, tau, nf in ((1, 1e-4, 1e-3, 1), (600, 1e-4, 1e-3, 1), (64, 0.0, 1e-3, 1), (64, 1e-4, -1.0, 1),
