@@ -54,14 +54,29 @@ def is_stale(debug: bool = False) -> bool:
 
 
 def build(force: bool = False, verbose: bool = False, extra_flags=None, debug: bool = False) -> str:
-    """Build libpat.so (debug: libpat_debug.so with the bounds checks) if needed and return its path."""
+    """Build libpat.so (debug: libpat_debug.so with the bounds checks) if needed and return its path.
+
+    Processes that build at the same time (the ranks of a multi-process launch) take turns on a
+    lock file; the first one builds and the others then find the library up to date.
+    """
+    import fcntl
     lib = LIB_DEBUG if debug else LIB
-    bdir = BUILD_DEBUG if debug else BUILD
     if not force and not is_stale(debug):
         return lib
+    os.makedirs(LIBDIR, exist_ok=True)
+    with open(os.path.join(LIBDIR, ".build.lock"), "w") as lock:
+        fcntl.flock(lock, fcntl.LOCK_EX)
+        try:
+            if not force and not is_stale(debug):
+                return lib
+            return _compile(lib, BUILD_DEBUG if debug else BUILD, verbose, extra_flags, debug)
+        finally:
+            fcntl.flock(lock, fcntl.LOCK_UN)
+
+
+def _compile(lib: str, bdir: str, verbose: bool, extra_flags, debug: bool) -> str:
     nvcc = _nvcc()
     os.makedirs(bdir, exist_ok=True)
-    os.makedirs(LIBDIR, exist_ok=True)
     flags = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--cudart", "shared",
                     "-I", os.path.join(ROOT, "include")] + (["-DPAT_DEBUG_BOUNDS"] if debug else []) + \
         list(extra_flags or [])
