@@ -42,6 +42,12 @@ def pat_forward(p0: torch.Tensor, c: torch.Tensor, plan: Plan) -> torch.Tensor:
 
 
 def data_misfit(y: torch.Tensor, y_meas: torch.Tensor, w: torch.Tensor) -> torch.Tensor:
-    """J = sum_k w_k / 2 ||y_k - y_meas_k||^2 (Eq. Minimised_functional, data term), FP64 sum."""
+    """J = sum_k w_k / 2 ||y_k - y_meas_k||^2 (Eq. Minimised_functional, data term), FP64 sum.
+
+    A loss for the differentiable path above, in torch operations on traces that the library
+    computed (its gradient dJ/dy = w_k (y_k - y_meas_k) becomes the adjoint source of pat_vjp).
+    The library evaluates the same J itself, with the gradient, in pat_adjoint_grad
+    (Plan.adjoint_grad); the reconstruction uses that one.
+    """
     d = (y - y_meas).double()
     return 0.5 * (w.double()[:, None, None] * d * d).sum()
