@@ -6,6 +6,11 @@ CUDA kernels of ``libpat.so`` (there is no CPU or PyTorch fallback).
 from __future__ import annotations
 
 import ctypes
+import dataclasses
+import hashlib
+import io
+import json
+import os
 from dataclasses import dataclass
 
 import numpy as np
@@ -395,7 +400,6 @@ def write_report_jsonl(rows, path, **fields):
     """Append one JSON line per L-BFGS iteration (level, iteration, J, |g|, step, trials, J after
     the step, wall ms, E_c, E_p0 as returned by reconstruct / reconstruct_batched) to path, each
     with the given extra fields (e.g. instance=3)."""
-    import json
     with open(path, "a") as f:
         for r in rows:
             f.write(json.dumps(dict(fields, **r)) + "\n")
@@ -477,9 +481,6 @@ def reconstruct(cfg: ReconConfig, y_meas, w, c_init, p0_init=None, stream=None, 
 
 def _fingerprint(cfg: ReconConfig, tensors) -> str:
     """Hash of the configuration and of the inputs a resumed run must share with the first."""
-    import dataclasses
-    import hashlib
-    import json
     h = hashlib.sha256()
     fields = {k: (np.asarray(v, dtype=np.float64).tolist() if k == "sensors_xy" else
                   [int(x) for x in v] if k == "levels" else v)
@@ -516,10 +517,6 @@ def reconstruct_resumable(cfg: ReconConfig, y_meas, w, c_init, state_path, p0_in
     Returns (c, p0, report rows, status, total_ms, levels_done); c and p0 are on the grid of the
     last level done (the finest once levels_done == len(cfg.levels)).
     """
-    import dataclasses
-    import io
-    import json
-    import os
     levels = [int(v) for v in cfg.levels]
     N = levels[-1]
     K = int(cfg.K)
