@@ -479,13 +479,15 @@ def reconstruct(cfg: ReconConfig, y_meas, w, c_init, p0_init=None, stream=None, 
     return c, p0, _rows(rep, rows), int(rep.status), float(rep.total_ms)
 
 
-def _fingerprint(cfg: ReconConfig, tensors) -> str:
-    """Hash of the configuration and of the inputs a resumed run must share with the first."""
+def _fingerprint(cfg: ReconConfig, tensors, extra=None) -> str:
+    """Hash of the configuration, the inputs and any extra JSON-able settings (targets) that a
+    resumed run must share with the first."""
     h = hashlib.sha256()
     fields = {k: (np.asarray(v, dtype=np.float64).tolist() if k == "sensors_xy" else
                   [int(x) for x in v] if k == "levels" else v)
               for k, v in dataclasses.asdict(cfg).items()}
     h.update(json.dumps(fields, sort_keys=True).encode())
+    h.update(json.dumps(extra).encode())
     for t in tensors:
         a = np.ascontiguousarray(t.detach().cpu().numpy())
         h.update(str(a.shape).encode())
@@ -496,65 +498,114 @@ def _fingerprint(cfg: ReconConfig, tensors) -> str:
 _ROW_FIELDS = ("level", "it", "J", "gnorm", "alpha", "trials", "J_new", "ms", "Ec", "Ep0")
 
 
-def reconstruct_resumable(cfg: ReconConfig, y_meas, w, c_init, state_path, p0_init=None, stop_after_level=None,
-                          stream=None, max_report=4096):
-    """Joint reconstruction that can stop after any multigrid level and continue later from a host file.
+def reconstruct_batched_resumable(cfg: ReconConfig, instances, state_path, stop_after_level=None, stream=None,
+                                  max_report=4096):
+    """Batched reconstructions (as reconstruct_batched) that can stop after any multigrid level and
+    continue later from a host file.
 
-    The schedule runs one level per pat_reconstruct call (levels=(N_l,)).  A level boundary is
-    where the method itself ends one optimisation and starts the next from the prolonged point
-    with an empty L-BFGS memory (Sec. 3.1), so the state there is the iterate alone: no curvature
-    pairs, and no random numbers (the reconstruction draws none).  After each level the state
-    (levels done, c and p0 on that level's grid, the report rows so far, status, wall time and a
-    fingerprint of cfg and the inputs) is written to ``state_path`` (an .npz, replaced
-    atomically).  Called with an existing state file it checks the fingerprint (ValueError if
-    cfg or any input differs) and continues with the next level: the first level's initial
-    guess and every level's start are the same bilinear transfers (pat_prolong) that
-    pat_reconstruct applies, and resampling onto the same grid inside the call is the identity,
-    so with the kernel variant fixed (cfg.autotune off) the result is bit-identical to one
-    pat_reconstruct over all levels.  ``stop_after_level`` = l returns after level l (an
-    interruption at a level boundary).
+    The schedule runs one level per pat_reconstruct_batched call (levels=(N_l,)).  A level
+    boundary is where the method itself ends one optimisation and starts the next from the
+    prolonged point with an empty L-BFGS memory (Sec. 3.1), so the state there is every
+    instance's iterate alone: no curvature pairs, and no random numbers (the reconstruction
+    draws none).  After each level the state (levels done; every instance's c and p0 on that
+    level's grid, report rows so far and status; the wall time; a fingerprint of cfg and of all
+    inputs and targets) is written to ``state_path`` (an .npz, replaced atomically).  Called with
+    an existing state file it checks the fingerprint (ValueError if cfg, an input or a target
+    differs) and continues with the next level.  Every level starts from the same bilinear
+    transfer (pat_prolong) that pat_reconstruct_batched applies between levels, the true c and
+    p0 of E_c / E_p0 tracking are resampled from the finest grid as it does, and resampling onto
+    the same grid inside a call is the identity, so with the kernel variants fixed (cfg.autotune
+    off) the results are bit-identical to one pat_reconstruct_batched call over all levels.
+    ``stop_after_level`` = l returns after level l (an interruption at a level boundary).
 
-    Returns (c, p0, report rows, status, total_ms, levels_done); c and p0 are on the grid of the
+    ``instances``: as for reconstruct_batched, on the finest grid.  Returns (a list of (c, p0,
+    report rows, status) per instance, total_ms, levels_done); c and p0 are on the grid of the
     last level done (the finest once levels_done == len(cfg.levels)).
     """
     levels = [int(v) for v in cfg.levels]
     N = levels[-1]
-    K = int(cfg.K)
-    dev = y_meas.device
-    p0_in = torch.zeros((K, N, N), dtype=torch.float32, device=dev) if p0_init is None else p0_init
-    _f32(c_init, (N, N), "c_init", dev)
-    _f32(p0_in, (K, N, N), "p0_init", dev)
-    fp = _fingerprint(cfg, (y_meas, w, c_init, p0_in))
-    done, rows, status, total = 0, [], 0, 0.0
-    c, p0 = c_init.detach().clone().contiguous(), p0_in.detach().clone().contiguous()
+    inputs, cur = [], []
+    for ins in instances:
+        ym = ins["y_meas"]
+        K, dev = int(ym.shape[0]), ym.device
+        p0 = ins.get("p0_init")
+        p0 = torch.zeros((K, N, N), dtype=torch.float32, device=dev) if p0 is None else p0
+        _f32(ins["c_init"], (N, N), "c_init", dev)
+        _f32(p0, (K, N, N), "p0_init", dev)
+        inputs += [ym, ins["w"], ins["c_init"], p0] + [ins[k] for k in ("c_true", "p0_true") if ins.get(k) is not None]
+        cur.append([ins["c_init"].detach().clone().contiguous(), p0.detach().clone().contiguous(), [], 0])
+    targets = [[float(ins.get("ec_target", 0.0)), float(ins.get("ep0_target", 0.0)),
+                ins.get("c_true") is not None, ins.get("p0_true") is not None] for ins in instances]
+    fp = _fingerprint(cfg, inputs, extra=targets)
+    done, total = 0, 0.0
     if os.path.exists(state_path):
         with np.load(state_path, allow_pickle=False) as z:
             meta = json.loads(str(z["meta"]))
             if meta["fingerprint"] != fp:
                 raise ValueError(f"{state_path}: saved by a run with another configuration or other inputs")
-            done, status, total = int(meta["levels_done"]), int(meta["status"]), float(meta["total_ms"])
-            rows = [dict(zip(_ROW_FIELDS, r)) for r in meta["rows"]]
-            c = torch.as_tensor(z["c"], device=dev).contiguous()
-            p0 = torch.as_tensor(z["p0"], device=dev).contiguous()
+            done, total = int(meta["levels_done"]), float(meta["total_ms"])
+            for i, st in enumerate(cur):
+                dev = instances[i]["y_meas"].device
+                st[0] = torch.as_tensor(z[f"c{i}"], device=dev).contiguous()
+                st[1] = torch.as_tensor(z[f"p0{i}"], device=dev).contiguous()
+                st[2] = [dict(zip(_ROW_FIELDS, r)) for r in meta["rows"][i]]
+                st[3] = int(meta["status"][i])
     last = len(levels) - 1 if stop_after_level is None else min(int(stop_after_level), len(levels) - 1)
     for li in range(done, last + 1):
         n_l = levels[li]
-        c_start = prolong(c.view(1, *c.shape), n_l, stream=stream)[0].contiguous()
-        p0_start = prolong(p0, n_l, stream=stream)
-        one = dataclasses.replace(cfg, levels=(n_l,))
-        c, p0, r, st, ms = reconstruct(one, y_meas, w, c_start, p0_start, stream=stream, max_report=max_report)
-        for row in r:
-            row["level"] = li
-        rows += r
-        status = st if st != 0 else status
+        lv = []
+        for ins, (c, p0, _, _) in zip(instances, cur):
+            d = {"y_meas": ins["y_meas"], "w": ins["w"],
+                 "c_init": prolong(c.view(1, *c.shape), n_l, stream=stream)[0].contiguous(),
+                 "p0_init": prolong(p0, n_l, stream=stream)}
+            if ins.get("c_true") is not None:
+                ct = ins["c_true"]
+                d["c_true"] = prolong(ct.view(1, *ct.shape), n_l, stream=stream)[0].contiguous()
+            if ins.get("p0_true") is not None:
+                d["p0_true"] = prolong(ins["p0_true"], n_l, stream=stream)
+            for k in ("ec_target", "ep0_target"):
+                if k in ins:
+                    d[k] = ins[k]
+            lv.append(d)
+        res, ms = reconstruct_batched(dataclasses.replace(cfg, levels=(n_l,)), lv, stream=stream,
+                                      max_report=max_report)
+        for st, (c, p0, rows, status) in zip(cur, res):
+            for row in rows:
+                row["level"] = li
+            st[0], st[1] = c, p0
+            st[2] = st[2] + rows
+            st[3] = status if status != 0 else st[3]
         total += ms
         done = li + 1
-        meta = {"fingerprint": fp, "levels_done": done, "levels": levels, "status": status, "total_ms": total,
-                "rows": [[row[k] for k in _ROW_FIELDS] for row in rows]}
+        meta = {"fingerprint": fp, "levels_done": done, "levels": levels, "total_ms": total,
+                "status": [st[3] for st in cur], "rows": [[[row[k] for k in _ROW_FIELDS] for row in st[2]] for st in cur]}
+        arrays = {}
+        for i, st in enumerate(cur):
+            arrays[f"c{i}"] = st[0].cpu().numpy()
+            arrays[f"p0{i}"] = st[1].cpu().numpy()
         buf = io.BytesIO()
-        np.savez(buf, c=c.cpu().numpy(), p0=p0.cpu().numpy(), meta=np.array(json.dumps(meta)))
+        np.savez(buf, meta=np.array(json.dumps(meta)), **arrays)
         tmp = f"{state_path}.tmp{os.getpid()}"
         with open(tmp, "wb") as f:
             f.write(buf.getvalue())
         os.replace(tmp, state_path)
+    return [tuple(st) for st in cur], total, done
+
+
+def reconstruct_resumable(cfg: ReconConfig, y_meas, w, c_init, state_path, p0_init=None, stop_after_level=None,
+                          stream=None, max_report=4096):
+    """Joint reconstruction (as reconstruct) that can stop after any multigrid level and continue
+    later from a host file: reconstruct_batched_resumable with one instance (pat_reconstruct is
+    pat_reconstruct_batched with one instance), so bit-identical to one uninterrupted
+    pat_reconstruct when the kernel variants are fixed.
+
+    Returns (c, p0, report rows, status, total_ms, levels_done); c and p0 are on the grid of the
+    last level done (the finest once levels_done == len(cfg.levels)).
+    """
+    ins = {"y_meas": y_meas, "w": w, "c_init": c_init}
+    if p0_init is not None:
+        ins["p0_init"] = p0_init
+    res, total, done = reconstruct_batched_resumable(cfg, [ins], state_path, stop_after_level=stop_after_level,
+                                                     stream=stream, max_report=max_report)
+    c, p0, rows, status = res[0]
     return c, p0, rows, status, total, done

@@ -65,3 +65,37 @@ def test_uninterrupted_resumable_run_matches_and_other_inputs_are_refused(tmp_pa
     assert done == 3 and torch.equal(c, c_ref) and torch.equal(p0, p0_ref)
     with pytest.raises(ValueError):
         reconstruct_resumable(cfg, y, 2.0 * wt, c0, path)
+
+
+def _instance(seed, with_truth=False, with_p0=False):
+    from oracle.forward import forward
+    from oracle.grid import make_grid
+    from oracle.sensors import sensor_matrix
+    w = ps.workload("plain64", seed)
+    g = make_grid(64, w.dx, 300, c_ref=1750.0)
+    y = ps.add_noise(forward(g, w.c_true, w.p0_true, sensor_matrix(g, w.sensors)), ps.rng_for(100 + seed))
+    ins = {"y_meas": _dev(y), "w": _dev(ps.noise_weights(y)),
+           "c_init": _dev(np.full((64, 64), 0.5 * (w.c_true.min() + w.c_true.max())))}
+    if with_truth:
+        ins.update(c_true=_dev(w.c_true), p0_true=_dev(w.p0_true), ec_target=2.5)
+    if with_p0:
+        ins["p0_init"] = _dev(0.25 * w.p0_true)
+    return ins
+
+
+def test_batched_resume_is_bit_identical(tmp_path):
+    from paper_2505_08482_gb300.solver import reconstruct_batched, reconstruct_batched_resumable
+    cfg, _, _, _ = _problem()
+    instances = [_instance(3), _instance(4, with_truth=True), _instance(5, with_p0=True)]
+    ref, _ = reconstruct_batched(cfg, instances)
+    path = str(tmp_path / "batch.npz")
+    part, _, done = reconstruct_batched_resumable(cfg, instances, path, stop_after_level=0)
+    assert done == 1 and all(tuple(c.shape) == (32, 32) for c, _, _, _ in part)
+    res, _, done = reconstruct_batched_resumable(cfg, instances, path)
+    assert done == 3
+    keys = KEYS + ("Ec", "Ep0")
+    for (c, p0, rows, st), (cr, p0r, rowsr, str_) in zip(res, ref):
+        assert torch.equal(c, cr) and torch.equal(p0, p0r) and st == str_
+        assert [[r[k] for k in keys] for r in rows] == [[r[k] for k in keys] for r in rowsr]
+    with pytest.raises(ValueError):
+        reconstruct_batched_resumable(cfg, instances[:2], path)
