@@ -119,6 +119,9 @@ def parse():
                     help="data sets of the default line's many-waves pass measurement (0: none)")
     ap.add_argument("--cluster", action="store_true",
                     help="with --roofline-k: forward sweeps in the cluster-resident form (pat_plan_set_cluster)")
+    ap.add_argument("--recon256", action="store_true",
+                    help="time to the E_c / E_p0 targets of one plain reconstruction at the headline workload "
+                         "(256^2, K=8, Nt=1800, levels 64->128->256)")
     ap.add_argument("--prior-cost", action="store_true",
                     help="cost of the Ornstein-Uhlenbeck prior terms on the headline grid (9 fields)")
     ap.add_argument("--table2", action="store_true",
@@ -755,6 +758,59 @@ def time_to_rel_err(args, dev):
             "speedup_batched_vs_plain": wall_plain / wall_b}
 
 
+def run_recon256(args):
+    """One plain reconstruction (pat_reconstruct through the batched call with one instance) of
+    the headline workload: 256 x 256 domain, K = 8 vessel p0 sets, M = 512 sensors, Nt = 1800,
+    s = 32, 1 % noise, levels 64 -> 128 -> 256 with at most ttr_iters L-BFGS iterations each,
+    c starting at the midpoint of the true range, p0 at zero.  E_c and E_p0 (Eq. RelativeError)
+    are tracked after every iteration against the true c and p0 resampled to the level; the run
+    leaves a level (the finest: stops) once both targets are met.  Prints the wall time, the
+    iterations and the time at which the targets were first met on the finest level."""
+    import numpy as np
+    import torch
+
+    import pat_synth as ps
+    import paper_2505_08482_gb300 as pkg
+    from paper_2505_08482_gb300.solver import GridSpec, Plan, ReconConfig, reconstruct_batched
+    pkg.build()
+    dev = torch.device("cuda", 0)
+    f32 = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float32, device=dev)
+    w, c_init = inputs(0)
+    n, K, M, nt = WL["n"], WL["K"], WL["M"], WL["nt"]
+    dx = WL["dx"]
+    gs = GridSpec(n=n, pml=pml_auto(n), dx=dx, dt=WL["cfl"] * dx / WL["c_hi"], nt=nt, c_ref=WL["c_hi"])
+    gen = Plan(gs, w.sensors, K, device=dev)
+    y = ps.add_noise(gen.forward(f32(w.c_true), f32(w.p0_true)).cpu().numpy(), ps.rng_for(500))
+    del gen
+    ins = dict(y_meas=f32(y), w=f32(ps.noise_weights(y)), c_init=f32(np.full((n, n), c_init)),
+               c_true=f32(w.c_true), p0_true=f32(w.p0_true), ec_target=args.ttr_ec, ep0_target=args.ttr_ep0)
+    cfg = ReconConfig(levels=(64, 128, 256), L=n * dx, dt_data=gs.dt, nt_data=nt, sensors_xy=w.sensors, K=K,
+                      iters=args.ttr_iters, mem=20, ckpt_every=WL["ckpt_every"], rtol=0.0)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    res, total_ms = reconstruct_batched(cfg, [ins])
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    rows = res[0][2]
+    fin = [r for r in rows if r["level"] == 2]
+    hit = next((i for i, r in enumerate(rows) if r["level"] == 2 and r["Ec"] <= args.ttr_ec
+                and r["Ep0"] <= args.ttr_ep0), None)
+    per_level = {str(cfg.levels[lv]): {"iterations": sum(1 for r in rows if r["level"] == lv),
+                                       "ms": sum(r["ms"] for r in rows if r["level"] == lv)} for lv in range(3)}
+    line = {"metric": "time to E_c / E_p0 targets, plain GPU reconstruction", "value": wall, "unit": "s",
+            "n_gpus": 1, "higher_is_better": False, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"{WL['workload']}: 256x256 (Ng 300), K={K}, M={M}, Nt={nt}, s={WL['ckpt_every']}, "
+                                   "levels 64->128->256, 1 % noise, c from the midpoint of the true range",
+                       "targets": {"E_c_pct": args.ttr_ec, "E_p0_pct": args.ttr_ep0,
+                                   "max_iterations_per_level": args.ttr_iters}},
+            "reached": hit is not None, "iterations": len(rows), "per_level": per_level,
+            "iteration_time_to_targets_s": None if hit is None else sum(r["ms"] for r in rows[:hit + 1]) / 1e3,
+            "E_c_initial_pct": float(100.0 * np.linalg.norm(c_init - w.c_true) / np.linalg.norm(w.c_true)),
+            "E_c_final_pct": fin[-1]["Ec"] if fin else None, "E_p0_final_pct": fin[-1]["Ep0"] if fin else None,
+            "status": res[0][3], "library_total_ms": total_ms}
+    print(json.dumps(line), flush=True)
+
+
 def warm_start_sample(args):
     """The learned warm start against the plain start on a reduced sample of its workload:
     the U-Net (4 levels x 32 channels, BF16 on the tcgen05 tensor cores) trained on
@@ -1363,6 +1419,9 @@ def main():
         return
     if args.prior_cost:
         run_prior_cost(args)
+        return
+    if args.recon256:
+        run_recon256(args)
         return
     if world > 1:
         import torch
