@@ -675,6 +675,8 @@ def run_ours(args, rank, world, local_rank):
                                                     "forward sweep that runs alone; variant from the autotuner"}
     if rank == 0 and world == 1 and not args.no_ttr:
         line["time_to_rel_err"] = time_to_rel_err(args, dev)
+        # the plain solve at the headline workload itself (256^2, K = 8, three levels)
+        line["time_to_rel_err"]["headline_plain"] = recon256(args, dev)
         if not args.no_ws_sample:
             line["time_to_rel_err"]["warm_start"] = warm_start_sample(args)
         if not args.no_table2_sample:
@@ -759,6 +761,13 @@ def time_to_rel_err(args, dev):
 
 
 def run_recon256(args):
+    import paper_2505_08482_gb300 as pkg
+    pkg.build()
+    import torch
+    print(json.dumps(recon256(args, torch.device("cuda", 0))), flush=True)
+
+
+def recon256(args, dev):
     """One plain reconstruction (pat_reconstruct through the batched call with one instance) of
     the headline workload: 256 x 256 domain, K = 8 vessel p0 sets, M = 512 sensors, Nt = 1800,
     s = 32, 1 % noise, levels 64 -> 128 -> 256 with at most ttr_iters L-BFGS iterations each,
@@ -770,10 +779,7 @@ def run_recon256(args):
     import torch
 
     import pat_synth as ps
-    import paper_2505_08482_gb300 as pkg
     from paper_2505_08482_gb300.solver import GridSpec, Plan, ReconConfig, reconstruct_batched
-    pkg.build()
-    dev = torch.device("cuda", 0)
     f32 = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float32, device=dev)
     w, c_init = inputs(0)
     n, K, M, nt = WL["n"], WL["K"], WL["M"], WL["nt"]
@@ -808,7 +814,7 @@ def run_recon256(args):
             "E_c_initial_pct": float(100.0 * np.linalg.norm(c_init - w.c_true) / np.linalg.norm(w.c_true)),
             "E_c_final_pct": fin[-1]["Ec"] if fin else None, "E_p0_final_pct": fin[-1]["Ep0"] if fin else None,
             "status": res[0][3], "library_total_ms": total_ms}
-    print(json.dumps(line), flush=True)
+    return line
 
 
 def warm_start_sample(args):
