@@ -773,8 +773,9 @@ def recon256(args, dev):
     s = 32, 1 % noise, levels 64 -> 128 -> 256 with at most ttr_iters L-BFGS iterations each,
     c starting at the midpoint of the true range, p0 at zero.  E_c and E_p0 (Eq. RelativeError)
     are tracked after every iteration against the true c and p0 resampled to the level; the run
-    leaves a level (the finest: stops) once both targets are met.  Prints the wall time, the
-    iterations and the time at which the targets were first met on the finest level."""
+    leaves a level (the finest: stops) once both targets are met.  Returns the line: wall time,
+    iterations per level and the iteration time until the targets were first met on the finest
+    level."""
     import numpy as np
     import torch
 
